@@ -1,0 +1,156 @@
+/*
+ * lbmp — C-ABI of the GB300 (sm_103a) site-based particle-suspension lattice Boltzmann
+ * library (dos Santos & Philippi, "An alternative method for simulating particle
+ * suspensions using lattice Boltzmann", arXiv:1105.2904).
+ *
+ * One time step (lbm_step) is, in the paper's order:
+ *   - BGK collision of every lattice site, solids included (Sec. 2.1, Eq. 3), with Guo
+ *     body forcing, fused with the pull-propagation of the previous step (Eq. 3 LHS);
+ *   - momentum transfer at each particle's boundary sites, BS (Sec. 2.2, Eqs. 5-7) and the
+ *     per-particle reduction of the exchanged momentum and angular momentum (Eqs. 8-9);
+ *   - particle acceleration (Eqs. 10-11) and hard-core particle-particle and
+ *     particle-wall collisions (Sec. 2.3, Eqs. 16-19);
+ *   - position update (Eqs. 13-15) and the re-marking of each particle's BS / IS sites;
+ *   - equilibrium imposition at the internal sites, IS (Eq. 12), applied as the next
+ *     step pulls its populations.
+ *
+ * Conventions shared by every call:
+ *   - Lattice units: dx = dt = 1. Sites are indexed x fastest: idx = x + nx*(y + ny*z).
+ *     D2Q9 uses nz = 1 and ignores z components of vectors (omega uses only z).
+ *   - Host arrays passed in or out are caller-owned, plain C arrays of double unless
+ *     stated; the library copies them synchronously and never keeps the pointers.
+ *     Device memory is owned by the library and freed by lbm_destroy.
+ *   - Distribution arrays are f[i][z][y][x] with i in the velocity order below.
+ *       D2Q9 : (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+ *       D3Q19: (0,0,0) (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1) (1,1,0) (-1,-1,0)
+ *              (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1)
+ *              (0,1,-1) (0,-1,1)
+ *   - Every call returns an lbm_status; none exits, traps or asserts on the device.
+ *     Kernels report faults (capacity overflow, a particle moving more than one site per
+ *     step, ...) through a device status word that lbm_synchronize and the getters read.
+ *     lbm_last_error gives a one-line description of the last non-OK status.
+ *   - The library fails loudly: if no CUDA device is usable, lbm_create returns
+ *     LBM_E_CUDA. There is no CPU fallback.
+ */
+#ifndef LBMP_H
+#define LBMP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_E_INVALID = 1,  /* bad argument (size, tau <= 1/2, radius, wall crossing, ...) */
+    LBM_E_OOM = 2,      /* device allocation failed */
+    LBM_E_CUDA = 3,     /* a CUDA call failed (no device, launch error, ...) */
+    LBM_E_OVERLAP = 4,  /* particles overlap when added */
+    LBM_E_TIMEOUT = 5,  /* a bounded device wait expired */
+    LBM_E_STATE = 6,    /* call not allowed in the current state (e.g. configure after step) */
+    LBM_E_NAN = 7,      /* non-finite value detected in the state */
+    LBM_E_CAPACITY = 8, /* a device work list overflowed (e.g. contact pairs) */
+    LBM_E_UNSTABLE = 9  /* a particle moved by more than one site in one step */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+
+/* Storage precision of the distributions. Arithmetic is FP64 for LBM_FP64 and FP32
+ * otherwise; particle state and force/torque sums are FP64 in every mode.
+ *   LBM_FP64    : f stored as is (the parity build; evaluates the same IEEE operations as
+ *                 a plain FP64 implementation, reductions in a fixed order);
+ *   LBM_FP32    : deviation g_i = f_i - w_i stored in FP32;
+ *   LBM_FP16DEV : (f_i - w_i)/w_i stored in IEEE half;
+ *   LBM_BF16DEV : (f_i - w_i)/w_i stored in bfloat16. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2, LBM_BF16DEV = 3 } lbm_precision;
+
+typedef enum { LBM_PERIODIC = 0, LBM_NOSLIP = 1 } lbm_face;
+
+/* Creates a simulation of an nx*ny*nz lattice (D2Q9: nz = 1) of BGK fluid with relaxation
+ * time tau (viscosity nu = (tau - 1/2)/3, Sec. 2.1 Eq. 4) at rest (f_i = w_i, rho = 1).
+ * body_force: force density F applied at every site by Guo forcing; may be NULL (zero).
+ * Defaults: LBM_FP32, all faces periodic, no particle gravity, contact gap 0, F not applied
+ * to particles, a library-created non-blocking stream.
+ * Errors: LBM_E_INVALID (sizes < 1, nz != 1 for D2Q9, tau <= 1/2, more than 2^31 sites),
+ *         LBM_E_CUDA (no usable device). *out is NULL on error. */
+lbm_status lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau,
+                      const double body_force[3]);
+
+/* Sets the storage precision (lbm_precision), the kind of each face (lbm_face; order -x,+x,
+ * -y,+y,-z,+z; both faces of an axis must agree; NULL = all periodic), the acceleration g of
+ * gravity on particles (net buoyant: (1 - 1/rho_p) g, Sec. 3.3-3.4 settling runs; NULL =
+ * none), the contact gap added to r_i + r_j in the hard-core trigger (Sec. 2.3), whether F
+ * also accelerates particles (F/rho_p), and the CUDA stream (cudaStream_t, may be NULL) on
+ * which every later call enqueues its work. Walls are halfway bounce-back planes at -1/2
+ * and n - 1/2 (the bounce-back solid of Sec. 3.1).
+ * Only allowed before particles are added, distributions set, or a step is taken
+ * (LBM_E_STATE). LBM_E_INVALID on a bad enum value or mismatched faces. */
+lbm_status lbm_configure(lbm_ctx* ctx, int precision, const int faces[6],
+                         const double particle_gravity[3], double contact_gap,
+                         int body_force_on_particles, void* cuda_stream);
+
+/* Adds n rigid spheres (disks for D2Q9) (Sec. 2.2: centre x_p, radius r_p, mass and
+ * moment of inertia from the density). centers, velocities and omegas are n*3 (xyz);
+ * radii and densities are n. densities are particle/fluid density ratios; +INFINITY makes
+ * a fixed particle that never moves. velocities / omegas may be NULL (zero).
+ * The particle's lattice sites are classified once, around the given centre, into BS
+ * (solid sites with a neighbour outside the sphere), IS (solid sites next to BS) and the
+ * rest, and this set then translates rigidly with the particle (Eqs. 14-15).
+ * *first_id (may be NULL) receives the id of the first added particle; ids are dense.
+ * Only before the first lbm_step (LBM_E_STATE). Errors: LBM_E_INVALID (radius < 1.5 or
+ * > 120, density <= 0, sphere wider than half a periodic axis, sphere crossing a wall),
+ * LBM_E_OVERLAP (two spheres overlap). On error nothing is added. */
+lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const double* radii,
+                             const double* densities, const double* velocities,
+                             const double* omegas, int* first_id);
+
+/* Enqueues n time steps on the context's stream (replays of a captured CUDA graph) and
+ * returns without waiting. Steps never leave the device. n = 0 is a no-op. */
+lbm_status lbm_step(lbm_ctx* ctx, int n);
+
+/* Waits for the context's stream and returns the device status word (LBM_OK, or the first
+ * fault a kernel recorded: LBM_E_CAPACITY, LBM_E_UNSTABLE, ...). */
+lbm_status lbm_synchronize(lbm_ctx* ctx);
+
+/* Macroscopic fields of the current state: rho[N] (Eq. 1) and u[N*3] (site-major, xyz)
+ * with rho u = sum_i f_i c_i + F/2 (Eq. 2 with the Guo half-force). Synchronizes. */
+lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u);
+
+/* Particle state after the last step, n*3 each (any pointer may be NULL): centre x_p
+ * (continuous, not wrapped into periodic boxes), velocity u_p, angular velocity omega_p,
+ * force = -dP_B and torque = -dL_B exchanged with the fluid in the last step (Eqs. 8-9,
+ * dt = 1). Synchronizes. */
+lbm_status lbm_get_particles(lbm_ctx* ctx, double* x, double* u, double* omega,
+                             double* force, double* torque);
+
+/* Full distribution state f[Q][N] at the current step boundary (post-propagation, with
+ * the IS imposition applied), converted to double. Synchronizes. */
+lbm_status lbm_get_distributions(lbm_ctx* ctx, double* f);
+
+/* Replaces the distribution state by f[Q][N] (same layout as lbm_get_distributions).
+ * Values are rounded to the storage precision. Synchronizes. */
+lbm_status lbm_set_distributions(lbm_ctx* ctx, const double* f);
+
+/* Owner map of the lattice sites, tags[N] (unsigned 32-bit): (class << 30) | particle id
+ * with class 0 = IS, 1 = BS, 2 = other solid site; 0xFFFFFFFF = fluid. Where the site
+ * sets of close particles meet, IS wins over BS over the rest, then the lower id.
+ * Synchronizes. */
+lbm_status lbm_get_masks(lbm_ctx* ctx, unsigned* tags);
+
+/* Introspection: out[0] = number of particles, out[1] = steps taken, out[2] = kernel
+ * launches per step in the captured graph, out[3] = device bytes held by the context,
+ * out[4] = bytes of distribution storage per site and step moved by the main sweep
+ * (2 Q b), out[5] = precision. Returns LBM_E_INVALID if out is NULL. */
+lbm_status lbm_get_info(lbm_ctx* ctx, long long out[6]);
+
+/* Description of the last non-OK status of ctx (static storage; never NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Frees every device and host resource of ctx (NULL is a no-op). Synchronizes first. */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMP_H */

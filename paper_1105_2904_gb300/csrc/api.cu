@@ -1,0 +1,745 @@
+// Host side of the C-ABI declared in include/lbmp.h: argument checks, device allocation,
+// particle set-up (classification of each particle's lattice sites, Sec. 2.2 / Fig. 2),
+// capture of one time step into CUDA graphs, and the synchronous getters/setters.
+// Host arithmetic that must agree with a plain FP64 implementation (site classification,
+// masses) is compiled with -ffp-contract=off.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels.h"
+#include "lbmp.h"
+
+using namespace lbmp;
+
+namespace {
+constexpr double LBM_PI = 3.14159265358979323846;
+constexpr int PAIR_CAP = 16384;
+constexpr size_t STAGING_BYTES = 64ull << 20;
+}  // namespace
+
+struct lbm_ctx {
+    int lattice = 1, Q = 19, D = 3;
+    Geom g{};
+    double tau = 0.6, F[3] = {0, 0, 0};
+    int precision = LBM_FP32;
+    const KernelTable* kt = nullptr;
+    double grav[3] = {0, 0, 0};
+    double gap = 0.0;
+    int bfp = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool allocated = false;
+    bool stepped = false;
+
+    void* f[2] = {nullptr, nullptr};
+    void* stash[2] = {nullptr, nullptr};
+    unsigned* tag = nullptr;
+    double* bs_scratch = nullptr;
+    int cur = 0;
+
+    int np = 0;
+    std::vector<PConst> h_pc;
+    std::vector<PKern> h_pk;
+    std::vector<double> h_x;
+    std::vector<int> h_tmpl;
+    PKern* pk = nullptr;
+    PConst* pc = nullptr;
+    int* tmpl = nullptr;
+    double *x = nullptr, *un = nullptr, *acc = nullptr, *force = nullptr;
+    int* Kold = nullptr;
+    Counters* cnt = nullptr;
+    int* status = nullptr;
+    int* pending = nullptr;
+    CellGrid cg{};
+    int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_cursor = nullptr,
+        *cell_items = nullptr;
+    unsigned long long* pairs = nullptr;
+    int *changed = nullptr, *restamp = nullptr, *restamp_flag = nullptr;
+
+    double* staging = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int launches_per_step = 0;
+    long long steps = 0;
+    size_t dev_bytes = 0;
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, LBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                       \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
+    } while (0)
+
+template <typename T>
+lbm_status dev_alloc(lbm_ctx* ctx, T** p, size_t bytes)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LBM_E_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " +
+                                        cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    ctx->dev_bytes += bytes;
+    *p = (T*)q;
+    return LBM_OK;
+}
+
+#define CS(call)                                 \
+    do {                                         \
+        lbm_status s_ = (call);                  \
+        if (s_ != LBM_OK) return s_;             \
+    } while (0)
+
+const KernelTable* table_for(int precision)
+{
+    switch (precision) {
+    case LBM_FP64: return kernels_f64();
+    case LBM_FP32: return kernels_f32();
+    case LBM_FP16DEV: return kernels_f16();
+    case LBM_BF16DEV: return kernels_bf16();
+    default: return nullptr;
+    }
+}
+
+int lat_c(int lattice, int i, int k) { return lattice == 0 ? D2Q9::c(i, k) : D3Q19::c(i, k); }
+
+lbm_status ensure_alloc(lbm_ctx* ctx)
+{
+    if (ctx->allocated) return LBM_OK;
+    ctx->kt = table_for(ctx->precision);
+    const size_t N = ctx->g.N;
+    const size_t fbytes = (size_t)ctx->Q * N * (size_t)ctx->kt->elem_bytes;
+    CS(dev_alloc(ctx, &ctx->f[0], fbytes));
+    CS(dev_alloc(ctx, &ctx->f[1], fbytes));
+    CS(dev_alloc(ctx, &ctx->status, sizeof(int)));
+    CS(dev_alloc(ctx, &ctx->pending, sizeof(int)));
+    CS(dev_alloc(ctx, &ctx->staging, STAGING_BYTES));
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(ctx->pending, 0, sizeof(int), ctx->stream));
+    ctx->kt->fill_rest(ctx->lattice, ctx->f[0], ctx->g.N, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->cur = 0;
+    ctx->allocated = true;
+    return LBM_OK;
+}
+
+// Classification of the solid sites of one particle around its initial centre (Sec. 2.2,
+// Fig. 2): S = {o : |o - phi|^2 <= r^2} (offsets o from floor(x0)); BS = sites of S with a
+// neighbour (model velocity set) outside S; IS = other sites of S with a neighbour in BS;
+// the rest of S is interior. Entries are emitted in z, y, x lexicographic order.
+void classify(int lattice, const double phi[3], double r, std::vector<int>& out)
+{
+    const int D = lattice == 0 ? 2 : 3, Q = lattice == 0 ? 9 : 19;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) {
+        lo[k] = (int)std::floor(phi[k] - r) - 1;
+        hi[k] = (int)std::ceil(phi[k] + r) + 1;
+    }
+    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    auto at = [&](int ox, int oy, int oz) { return ((size_t)(oz - lo[2]) * ey + (oy - lo[1])) * ex + (ox - lo[0]); };
+    std::vector<unsigned char> inS((size_t)ex * ey * ez, 0), cls((size_t)ex * ey * ez, 0);
+    const double r2 = r * r;
+    for (int oz = lo[2]; oz <= hi[2]; ++oz)
+        for (int oy = lo[1]; oy <= hi[1]; ++oy)
+            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+                const double dx = (double)ox - phi[0];
+                const double dy = (double)oy - phi[1];
+                const double dz = (double)oz - phi[2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                inS[at(ox, oy, oz)] = d2 <= r2;
+            }
+    for (int oz = lo[2]; oz <= hi[2]; ++oz)
+        for (int oy = lo[1]; oy <= hi[1]; ++oy)
+            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+                if (!inS[at(ox, oy, oz)]) continue;
+                for (int i = 1; i < Q; ++i)
+                    if (!inS[at(ox + lat_c(lattice, i, 0), oy + lat_c(lattice, i, 1), oz + lat_c(lattice, i, 2))]) {
+                        cls[at(ox, oy, oz)] = 1;  // BS
+                        break;
+                    }
+            }
+    for (int oz = lo[2]; oz <= hi[2]; ++oz)
+        for (int oy = lo[1]; oy <= hi[1]; ++oy)
+            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+                const size_t b = at(ox, oy, oz);
+                if (!inS[b] || cls[b] == 1) continue;
+                bool is = false;
+                for (int i = 1; i < Q && !is; ++i)
+                    is = cls[at(ox + lat_c(lattice, i, 0), oy + lat_c(lattice, i, 1), oz + lat_c(lattice, i, 2))] == 1;
+                cls[b] = is ? 2 : 3;
+            }
+    out.clear();
+    for (int oz = lo[2]; oz <= hi[2]; ++oz)
+        for (int oy = lo[1]; oy <= hi[1]; ++oy)
+            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+                const size_t b = at(ox, oy, oz);
+                if (!inS[b]) continue;
+                const unsigned c = cls[b] == 1 ? CLS_BS : (cls[b] == 2 ? CLS_IS : CLS_IN);
+                out.push_back(tmpl_pack(ox, oy, oz, c));
+            }
+}
+
+double min_image_h(double d, int n, bool periodic)
+{
+    if (!periodic) return d;
+    return d - (double)n * std::floor(d / (double)n + 0.5);
+}
+
+int axis_n(const lbm_ctx* c, int k) { return k == 0 ? c->g.nx : (k == 1 ? c->g.ny : c->g.nz); }
+
+ParticleArgs particle_args(lbm_ctx* ctx)
+{
+    ParticleArgs a{};
+    a.lattice = ctx->lattice;
+    a.g = ctx->g;
+    a.np = ctx->np;
+    a.pk = ctx->pk;
+    a.pc = ctx->pc;
+    a.tmpl = ctx->tmpl;
+    a.tag = ctx->tag;
+    a.x = ctx->x;
+    a.Kold = ctx->Kold;
+    a.un = ctx->un;
+    a.acc = ctx->acc;
+    a.force = ctx->force;
+    a.bs_scratch = ctx->bs_scratch;
+    a.cnt = ctx->cnt;
+    a.status = ctx->status;
+    a.pending = ctx->pending;
+    a.cg = ctx->cg;
+    a.cell_of = ctx->cell_of;
+    a.cell_count = ctx->cell_count;
+    a.cell_start = ctx->cell_start;
+    a.cell_cursor = ctx->cell_cursor;
+    a.cell_items = ctx->cell_items;
+    a.pairs = ctx->pairs;
+    a.pair_cap = PAIR_CAP;
+    a.changed = ctx->changed;
+    a.restamp = ctx->restamp;
+    a.restamp_flag = ctx->restamp_flag;
+    a.gap = ctx->gap;
+    return a;
+}
+
+PartView part_view(lbm_ctx* ctx)
+{
+    PartView v{};
+    v.tag = ctx->np > 0 ? ctx->tag : nullptr;
+    v.pk = ctx->pk;
+    v.pending = ctx->pending;
+    return v;
+}
+
+// One time step on ctx->stream, reading buffer c and writing buffer 1 - c.
+int enqueue_step(lbm_ctx* ctx, int c)
+{
+    SweepArgs a{};
+    a.lattice = ctx->lattice;
+    a.g = ctx->g;
+    a.fin = ctx->f[c];
+    a.fout = ctx->f[1 - c];
+    a.pv = part_view(ctx);
+    a.stash_in = ctx->stash[c];
+    a.stash_out = ctx->stash[1 - c];
+    a.acc = ctx->acc;
+    a.bs_scratch = ctx->bs_scratch;
+    a.omega = 1.0 / ctx->tau;
+    a.pre = 1.0 - 0.5 / ctx->tau;
+    for (int k = 0; k < 3; ++k) a.F[k] = ctx->F[k];
+    ctx->kt->sweep(a, ctx->stream);
+    int launches = 1;
+    if (ctx->np > 0) {
+        launches += launch_particle_phase(particle_args(ctx), ctx->stream);
+        StashFixArgs s{};
+        s.lattice = ctx->lattice;
+        s.g = ctx->g;
+        s.fout = ctx->f[1 - c];
+        s.stash_out = ctx->stash[1 - c];
+        s.pk = ctx->pk;
+        s.pc = ctx->pc;
+        s.tmpl = ctx->tmpl;
+        s.list = ctx->changed;
+        s.cnt = ctx->cnt;
+        ctx->kt->stash_fix(s, ctx->stream);
+        ++launches;
+    }
+    return launches;
+}
+
+lbm_status build_graphs(lbm_ctx* ctx)
+{
+    for (int c = 0; c < 2; ++c) {
+        if (ctx->gexec[c]) continue;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const int launches = enqueue_step(ctx, c);
+        cudaError_t le = cudaGetLastError();
+        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+        if (le != cudaSuccess) return cuda_fail(ctx, le, "kernel launch during capture");
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+        cudaError_t ie = cudaGraphInstantiate(&ctx->gexec[c], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+        ctx->launches_per_step = launches;
+    }
+    return LBM_OK;
+}
+
+lbm_status sync_status(lbm_ctx* ctx)
+{
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->allocated) return LBM_OK;
+    int st = 0;
+    CK(cudaMemcpy(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st == ERR_CAPACITY) return fail(ctx, LBM_E_CAPACITY, "a device work list overflowed (contact pairs)");
+    if (st == ERR_UNSTABLE)
+        return fail(ctx, LBM_E_UNSTABLE, "a particle moved by more than one lattice site in one step");
+    if (st != 0) return fail(ctx, (lbm_status)st, "device status " + std::to_string(st));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double tau, const double body_force[3])
+{
+    if (!out) return LBM_E_INVALID;
+    *out = nullptr;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return LBM_E_INVALID;
+    if (nx < 1 || ny < 1 || nz < 1 || ny > 65535 || nz > 65535) return LBM_E_INVALID;
+    if (lattice == LBM_D2Q9 && nz != 1) return LBM_E_INVALID;
+    if (!(tau > 0.5) || !std::isfinite(tau)) return LBM_E_INVALID;
+    const unsigned long long N = (unsigned long long)nx * ny * nz;
+    if (N >= (1ull << 31)) return LBM_E_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return LBM_E_CUDA;
+    }
+    lbm_ctx* ctx = new lbm_ctx();
+    ctx->lattice = lattice;
+    ctx->Q = lattice == 0 ? 9 : 19;
+    ctx->D = lattice == 0 ? 2 : 3;
+    ctx->g.nx = nx;
+    ctx->g.ny = ny;
+    ctx->g.nz = nz;
+    ctx->g.N = (unsigned)N;
+    ctx->tau = tau;
+    for (int k = 0; k < 3; ++k) ctx->F[k] = body_force ? body_force[k] : 0.0;
+    if (lattice == 0) ctx->F[2] = 0.0;
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return LBM_E_CUDA;
+    }
+    ctx->own_stream = true;
+    *out = ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_configure(lbm_ctx* ctx, int precision, const int faces[6], const double particle_gravity[3],
+                         double contact_gap, int body_force_on_particles, void* cuda_stream)
+{
+    if (!ctx) return LBM_E_INVALID;
+    if (ctx->allocated || ctx->np > 0 || ctx->stepped)
+        return fail(ctx, LBM_E_STATE, "lbm_configure must precede particles, distributions and steps");
+    if (!table_for(precision)) return fail(ctx, LBM_E_INVALID, "unknown precision");
+    int walls[3] = {0, 0, 0};
+    if (faces) {
+        for (int k = 0; k < 3; ++k) {
+            if ((faces[2 * k] != LBM_PERIODIC && faces[2 * k] != LBM_NOSLIP) || faces[2 * k] != faces[2 * k + 1])
+                return fail(ctx, LBM_E_INVALID, "both faces of an axis must be the same kind");
+            walls[k] = faces[2 * k] == LBM_NOSLIP;
+        }
+    }
+    if (ctx->D == 2) walls[2] = 0;
+    if (!std::isfinite(contact_gap)) return fail(ctx, LBM_E_INVALID, "contact gap must be finite");
+    ctx->precision = precision;
+    for (int k = 0; k < 3; ++k) {
+        ctx->g.wall[k] = walls[k];
+        ctx->grav[k] = particle_gravity ? particle_gravity[k] : 0.0;
+    }
+    if (ctx->D == 2) ctx->grav[2] = 0.0;
+    ctx->gap = contact_gap;
+    ctx->bfp = body_force_on_particles ? 1 : 0;
+    if (cuda_stream) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        ctx->stream = (cudaStream_t)cuda_stream;
+        ctx->own_stream = false;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const double* radii,
+                             const double* densities, const double* velocities, const double* omegas,
+                             int* first_id)
+{
+    if (!ctx) return LBM_E_INVALID;
+    if (ctx->stepped) return fail(ctx, LBM_E_STATE, "particles must be added before the first step");
+    if (n < 0 || (n > 0 && (!centers || !radii || !densities)))
+        return fail(ctx, LBM_E_INVALID, "null particle arrays");
+    if ((long long)ctx->np + n >= (long long)PID_MASK) return fail(ctx, LBM_E_INVALID, "too many particles");
+    if (n == 0) {
+        if (first_id) *first_id = ctx->np;
+        return LBM_OK;
+    }
+    CS(ensure_alloc(ctx));
+    const int D = ctx->D;
+    std::vector<PConst> pc(n);
+    std::vector<PKern> pk(n);
+    std::vector<double> xs(3 * (size_t)n);
+    for (int q = 0; q < n; ++q) {
+        PConst& c = pc[q];
+        PKern& k = pk[q];
+        std::memset(&c, 0, sizeof(c));
+        std::memset(&k, 0, sizeof(k));
+        const double r = radii[q], rho = densities[q];
+        if (!(r >= 1.5) || !(r <= 120.0)) return fail(ctx, LBM_E_INVALID, "radius must lie in [1.5, 120]");
+        if (!(rho > 0.0)) return fail(ctx, LBM_E_INVALID, "density must be positive");
+        c.r = r;
+        for (int a = 0; a < 3; ++a) {
+            c.x0[a] = a < D ? centers[3 * q + a] : 0.0;
+            if (!std::isfinite(c.x0[a])) return fail(ctx, LBM_E_INVALID, "non-finite centre");
+            c.A[a] = (int)std::floor(c.x0[a]);
+            k.phi[a] = c.x0[a] - (double)c.A[a];
+            k.K[a] = c.A[a];
+            k.u[a] = (velocities && a < D) ? velocities[3 * q + a] : 0.0;
+            k.om[a] = omegas ? omegas[3 * q + a] : 0.0;
+            if (D == 2 && a < 2) k.om[a] = 0.0;
+            xs[3 * (size_t)q + a] = c.x0[a];
+        }
+        for (int a = 0; a < D; ++a) {
+            const int na = axis_n(ctx, a);
+            if (ctx->g.wall[a]) {
+                if (c.x0[a] + 0.5 < r || ((double)na - 0.5) - c.x0[a] < r)
+                    return fail(ctx, LBM_E_INVALID, "particle crosses a wall");
+            } else if (2.0 * (r + 2.0) >= (double)na) {
+                return fail(ctx, LBM_E_INVALID, "particle wider than half the periodic box");
+            }
+        }
+        // Continuum mass and moment of inertia of a sphere (3D) or disk (2D).
+        if (std::isinf(rho)) {
+            c.inv_m = 0.0;
+            c.inv_I = 0.0;
+            for (int a = 0; a < 3; ++a) c.ext[a] = 0.0;
+        } else {
+            const double vol = D == 3 ? (4.0 / 3.0) * LBM_PI * r * r * r : LBM_PI * r * r;
+            const double m = rho * vol;
+            const double I = D == 3 ? 0.4 * m * r * r : 0.5 * m * r * r;
+            const double inv_rho = 1.0 / rho;
+            c.inv_m = 1.0 / m;
+            c.inv_I = 1.0 / I;
+            for (int a = 0; a < 3; ++a)
+                c.ext[a] = ctx->grav[a] * (1.0 - inv_rho) + (ctx->bfp ? ctx->F[a] * inv_rho : 0.0);
+        }
+    }
+    // Hard-core particles may not overlap (Sec. 2.3).
+    std::vector<double> allx(ctx->h_x);
+    allx.insert(allx.end(), xs.begin(), xs.end());
+    std::vector<double> allr;
+    for (auto& c : ctx->h_pc) allr.push_back(c.r);
+    for (auto& c : pc) allr.push_back(c.r);
+    const int tot = ctx->np + n;
+    for (int i = ctx->np; i < tot; ++i)
+        for (int j = 0; j < i; ++j) {
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double d = min_image_h(allx[3 * (size_t)i + a] - allx[3 * (size_t)j + a], axis_n(ctx, a),
+                                             a < D && !ctx->g.wall[a]);
+                d2 += d * d;
+            }
+            const double R = allr[i] + allr[j];
+            if (d2 < R * R) return fail(ctx, LBM_E_OVERLAP, "particles " + std::to_string(j) + " and " +
+                                                                std::to_string(i) + " overlap");
+        }
+    // Site classification of each new particle (independent, spread over host threads).
+    std::vector<std::vector<int>> tm(n);
+    {
+        const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t)
+            th.emplace_back([&, t]() {
+                for (int q = (int)t; q < n; q += (int)nt) classify(ctx->lattice, pk[q].phi, pc[q].r, tm[q]);
+            });
+        for (auto& t : th) t.join();
+    }
+    for (int q = 0; q < n; ++q) {
+        pc[q].tmpl_off = (int)ctx->h_tmpl.size();
+        pc[q].tmpl_n = (int)tm[q].size();
+        ctx->h_tmpl.insert(ctx->h_tmpl.end(), tm[q].begin(), tm[q].end());
+        if (ctx->h_tmpl.size() >= (1ull << 31)) return fail(ctx, LBM_E_INVALID, "too many particle sites");
+    }
+    ctx->h_pc.insert(ctx->h_pc.end(), pc.begin(), pc.end());
+    ctx->h_pk.insert(ctx->h_pk.end(), pk.begin(), pk.end());
+    ctx->h_x.insert(ctx->h_x.end(), xs.begin(), xs.end());
+    const int first = ctx->np;
+    ctx->np = tot;
+
+    // (Re)build the device-side particle arrays.
+    CK(cudaStreamSynchronize(ctx->stream));
+    auto release = [&](void* p) {
+        if (!p) return;
+        auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+        if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+        cudaFree(p);
+    };
+    for (void* p : {(void*)ctx->pk, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->un,
+                    (void*)ctx->acc, (void*)ctx->force, (void*)ctx->Kold, (void*)ctx->cell_of,
+                    (void*)ctx->cell_count, (void*)ctx->cell_start, (void*)ctx->cell_cursor,
+                    (void*)ctx->cell_items, (void*)ctx->changed, (void*)ctx->restamp,
+                    (void*)ctx->restamp_flag})
+        release(p);
+    const size_t np = (size_t)ctx->np;
+    CS(dev_alloc(ctx, &ctx->pk, sizeof(PKern) * np));
+    CS(dev_alloc(ctx, &ctx->pc, sizeof(PConst) * np));
+    CS(dev_alloc(ctx, &ctx->tmpl, sizeof(int) * ctx->h_tmpl.size()));
+    CS(dev_alloc(ctx, &ctx->x, sizeof(double) * 3 * np));
+    CS(dev_alloc(ctx, &ctx->un, sizeof(double) * 3 * np));
+    CS(dev_alloc(ctx, &ctx->acc, sizeof(double) * 6 * np));
+    CS(dev_alloc(ctx, &ctx->force, sizeof(double) * 6 * np));
+    CS(dev_alloc(ctx, &ctx->Kold, sizeof(int) * 3 * np));
+    CS(dev_alloc(ctx, &ctx->cell_of, sizeof(int) * np));
+    CS(dev_alloc(ctx, &ctx->cell_items, sizeof(int) * np));
+    CS(dev_alloc(ctx, &ctx->changed, sizeof(int) * np));
+    CS(dev_alloc(ctx, &ctx->restamp, sizeof(int) * np));
+    CS(dev_alloc(ctx, &ctx->restamp_flag, sizeof(int) * np));
+    if (!ctx->tag) {
+        CS(dev_alloc(ctx, &ctx->tag, sizeof(unsigned) * (size_t)ctx->g.N));
+        CS(dev_alloc(ctx, &ctx->stash[0], (size_t)ctx->kt->compute_bytes * ctx->g.N));
+        CS(dev_alloc(ctx, &ctx->stash[1], (size_t)ctx->kt->compute_bytes * ctx->g.N));
+        CS(dev_alloc(ctx, &ctx->cnt, sizeof(Counters)));
+        CS(dev_alloc(ctx, &ctx->pairs, sizeof(unsigned long long) * PAIR_CAP));
+        if (ctx->precision == LBM_FP64)
+            CS(dev_alloc(ctx, &ctx->bs_scratch, sizeof(double) * 6 * (size_t)ctx->g.N));
+        CK(prepare_particle_kernels(PAIR_CAP));
+    }
+    // Cell grid for contact and neighbour searches: cells at least 2 r_max + gap + 4 wide.
+    double rmax = 0.0;
+    for (auto& c : ctx->h_pc) rmax = std::max(rmax, c.r);
+    const double h = 2.0 * rmax + std::max(ctx->gap, 0.0) + 4.0;
+    ctx->cg.total = 1;
+    for (int a = 0; a < 3; ++a) {
+        const int na = axis_n(ctx, a);
+        ctx->cg.n[a] = a < D ? std::max(1, (int)std::floor((double)na / h)) : 1;
+        ctx->cg.size[a] = a < D ? (double)na / ctx->cg.n[a] : 1e300;
+        ctx->cg.total *= ctx->cg.n[a];
+    }
+    CS(dev_alloc(ctx, &ctx->cell_count, sizeof(int) * (size_t)ctx->cg.total));
+    CS(dev_alloc(ctx, &ctx->cell_start, sizeof(int) * ((size_t)ctx->cg.total + 1)));
+    CS(dev_alloc(ctx, &ctx->cell_cursor, sizeof(int) * (size_t)ctx->cg.total));
+
+    CK(cudaMemcpyAsync(ctx->pk, ctx->h_pk.data(), sizeof(PKern) * np, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pc, ctx->h_pc.data(), sizeof(PConst) * np, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->tmpl, ctx->h_tmpl.data(), sizeof(int) * ctx->h_tmpl.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->x, ctx->h_x.data(), sizeof(double) * 3 * np, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 6 * np, ctx->stream));
+    CK(cudaMemsetAsync(ctx->force, 0, sizeof(double) * 6 * np, ctx->stream));
+    CK(cudaMemsetAsync(ctx->tag, 0xFF, sizeof(unsigned) * (size_t)ctx->g.N, ctx->stream));
+    launch_stamp_all(particle_args(ctx), ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < 2; ++c)
+        if (ctx->gexec[c]) {
+            cudaGraphExecDestroy(ctx->gexec[c]);
+            ctx->gexec[c] = nullptr;
+        }
+    if (first_id) *first_id = first;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int n)
+{
+    if (!ctx) return LBM_E_INVALID;
+    if (n < 0) return fail(ctx, LBM_E_INVALID, "negative step count");
+    if (n == 0) return LBM_OK;
+    CS(ensure_alloc(ctx));
+    CS(build_graphs(ctx));
+    ctx->stepped = true;
+    for (int s = 0; s < n; ++s) {
+        CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream));
+        ctx->cur ^= 1;
+        ++ctx->steps;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx* ctx)
+{
+    if (!ctx) return LBM_E_INVALID;
+    return sync_status(ctx);
+}
+
+static lbm_status materialize(lbm_ctx* ctx, int mode, double* out_a, double* out_b)
+{
+    CS(ensure_alloc(ctx));
+    CS(sync_status(ctx));
+    const size_t N = ctx->g.N;
+    const size_t per_site = mode == 0 ? 4 : (size_t)ctx->Q;
+    const size_t chunk = std::min(N, STAGING_BYTES / (per_site * sizeof(double)));
+    for (size_t s0 = 0; s0 < N; s0 += chunk) {
+        const size_t cnt = std::min(chunk, N - s0);
+        MaterializeArgs a{};
+        a.lattice = ctx->lattice;
+        a.g = ctx->g;
+        a.fin = ctx->f[ctx->cur];
+        a.pv = part_view(ctx);
+        a.stash_in = ctx->stash[ctx->cur];
+        for (int k = 0; k < 3; ++k) a.F[k] = ctx->F[k];
+        a.s0 = (unsigned)s0;
+        a.count = (unsigned)cnt;
+        a.mode = mode;
+        a.out0 = ctx->staging;
+        a.out1 = ctx->staging + cnt;
+        ctx->kt->materialize(a, ctx->stream);
+        CK(cudaGetLastError());
+        if (mode == 0) {
+            if (out_a) CK(cudaMemcpyAsync(out_a + s0, ctx->staging, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+            if (out_b)
+                CK(cudaMemcpyAsync(out_b + 3 * s0, ctx->staging + cnt, sizeof(double) * 3 * cnt,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+        } else {
+            for (int i = 0; i < ctx->Q; ++i)
+                CK(cudaMemcpyAsync(out_a + (size_t)i * N + s0, ctx->staging + (size_t)i * cnt, sizeof(double) * cnt,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u)
+{
+    if (!ctx) return LBM_E_INVALID;
+    return materialize(ctx, 0, rho, u);
+}
+
+lbm_status lbm_get_distributions(lbm_ctx* ctx, double* f)
+{
+    if (!ctx || !f) return LBM_E_INVALID;
+    return materialize(ctx, 1, f, nullptr);
+}
+
+lbm_status lbm_set_distributions(lbm_ctx* ctx, const double* f)
+{
+    if (!ctx || !f) return LBM_E_INVALID;
+    CS(ensure_alloc(ctx));
+    CS(sync_status(ctx));
+    const size_t N = ctx->g.N;
+    const size_t chunk = std::min(N, STAGING_BYTES / ((size_t)ctx->Q * sizeof(double)));
+    void* tmp = ctx->f[1 - ctx->cur];
+    for (size_t s0 = 0; s0 < N; s0 += chunk) {
+        const size_t cnt = std::min(chunk, N - s0);
+        for (int i = 0; i < ctx->Q; ++i)
+            CK(cudaMemcpyAsync(ctx->staging + (size_t)i * cnt, f + (size_t)i * N + s0, sizeof(double) * cnt,
+                               cudaMemcpyHostToDevice, ctx->stream));
+        ConvertArgs a{};
+        a.lattice = ctx->lattice;
+        a.g = ctx->g;
+        a.f = ctx->staging;
+        a.dst = tmp;
+        a.s0 = (unsigned)s0;
+        a.count = (unsigned)cnt;
+        ctx->kt->convert_in(a, ctx->stream);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    UnstreamArgs u{};
+    u.lattice = ctx->lattice;
+    u.g = ctx->g;
+    u.src = tmp;
+    u.dst = ctx->f[ctx->cur];
+    ctx->kt->unstream(u, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(ctx->pending, 0, sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_particles(lbm_ctx* ctx, double* x, double* u, double* omega, double* force, double* torque)
+{
+    if (!ctx) return LBM_E_INVALID;
+    CS(sync_status(ctx));
+    const size_t np = (size_t)ctx->np;
+    if (np == 0) return LBM_OK;
+    std::vector<PKern> pk(np);
+    std::vector<double> fo(6 * np);
+    CK(cudaMemcpy(pk.data(), ctx->pk, sizeof(PKern) * np, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(fo.data(), ctx->force, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost));
+    if (x) CK(cudaMemcpy(x, ctx->x, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost));
+    for (size_t p = 0; p < np; ++p)
+        for (int k = 0; k < 3; ++k) {
+            if (u) u[3 * p + k] = pk[p].u[k];
+            if (omega) omega[3 * p + k] = pk[p].om[k];
+            if (force) force[3 * p + k] = fo[6 * p + k];
+            if (torque) torque[3 * p + k] = fo[6 * p + 3 + k];
+        }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_masks(lbm_ctx* ctx, unsigned* tags)
+{
+    if (!ctx || !tags) return LBM_E_INVALID;
+    CS(sync_status(ctx));
+    if (ctx->np == 0 || !ctx->tag) {
+        std::memset(tags, 0xFF, sizeof(unsigned) * (size_t)ctx->g.N);
+        return LBM_OK;
+    }
+    CK(cudaMemcpy(tags, ctx->tag, sizeof(unsigned) * (size_t)ctx->g.N, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_ctx* ctx, long long out[6])
+{
+    if (!ctx || !out) return LBM_E_INVALID;
+    const int eb = table_for(ctx->precision)->elem_bytes;
+    if (!ctx->gexec[0] && ctx->allocated) build_graphs(ctx);
+    out[0] = ctx->np;
+    out[1] = ctx->steps;
+    out[2] = ctx->launches_per_step;
+    out[3] = (long long)ctx->dev_bytes;
+    out[4] = 2LL * ctx->Q * eb;
+    out[5] = ctx->precision;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+void lbm_destroy(lbm_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int c = 0; c < 2; ++c)
+        if (ctx->gexec[c]) cudaGraphExecDestroy(ctx->gexec[c]);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+}  // extern "C"

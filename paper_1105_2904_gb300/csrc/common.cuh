@@ -1,0 +1,183 @@
+// Shared definitions of the CUDA path: lattice velocity sets, storage formats, the owner
+// (tag) encoding and the device-side particle records.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmp {
+
+// ---- lattice velocity sets (D2Q9 of Fig. 1; D3Q19 for 3D) --------------------------------
+// Velocity order is part of the C-ABI (include/lbmp.h).
+struct D2Q9 {
+    static constexpr int Q = 9;
+    static constexpr int D = 2;
+    __host__ __device__ static constexpr int c(int i, int k)
+    {
+        constexpr int t[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                 {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+        return t[i][k];
+    }
+    __host__ __device__ static constexpr int opp(int i)
+    {
+        constexpr int t[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+        return t[i];
+    }
+    __host__ __device__ static constexpr double w(int i)
+    {
+        return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+struct D3Q19 {
+    static constexpr int Q = 19;
+    static constexpr int D = 3;
+    __host__ __device__ static constexpr int c(int i, int k)
+    {
+        constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                  {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return t[i][k];
+    }
+    __host__ __device__ static constexpr int opp(int i)
+    {
+        constexpr int t[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+        return t[i];
+    }
+    __host__ __device__ static constexpr double w(int i)
+    {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+// ---- storage formats -------------------------------------------------------------------
+// double : f itself (FP64 arithmetic).
+// float  : g = f - w_i (FP32 arithmetic on deviations).
+// half / bfloat16 : h = (f - w_i) / w_i, converted to g = h * w_i for FP32 arithmetic.
+template <typename S> struct Store;
+template <> struct Store<double> {
+    using C = double;
+    static constexpr bool deviation = false;
+    __device__ static double load(double v, double) { return v; }
+    __device__ static double save(double v, double) { return v; }
+};
+template <> struct Store<float> {
+    using C = float;
+    static constexpr bool deviation = true;
+    __device__ static float load(float v, float) { return v; }
+    __device__ static float save(float v, float) { return v; }
+};
+template <> struct Store<__half> {
+    using C = float;
+    static constexpr bool deviation = true;
+    __device__ static float load(__half v, float w) { return __half2float(v) * w; }
+    __device__ static __half save(float g, float w) { return __float2half_rn(g * (1.0f / w)); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using C = float;
+    static constexpr bool deviation = true;
+    __device__ static float load(__nv_bfloat16 v, float w) { return __bfloat162float(v) * w; }
+    __device__ static __nv_bfloat16 save(float g, float w)
+    {
+        return __float2bfloat16_rn(g * (1.0f / w));
+    }
+};
+
+// ---- owner map ---------------------------------------------------------------------------
+// tag = (class << 30) | particle id; the lowest value owns a site (IS < BS < IN < fluid).
+constexpr unsigned CLS_IS = 0u;
+constexpr unsigned CLS_BS = 1u;
+constexpr unsigned CLS_IN = 2u;
+constexpr unsigned TAG_FLUID = 0xFFFFFFFFu;
+constexpr unsigned PID_MASK = (1u << 30) - 1u;
+
+// Template entry: int8 offsets (x, y, z) from floor(x_p0) and the class, packed in 32 bits.
+__host__ __device__ inline int tmpl_ox(int e) { return (int)(signed char)(e & 0xFF); }
+__host__ __device__ inline int tmpl_oy(int e) { return (int)(signed char)((e >> 8) & 0xFF); }
+__host__ __device__ inline int tmpl_oz(int e) { return (int)(signed char)((e >> 16) & 0xFF); }
+__host__ __device__ inline unsigned tmpl_cls(int e) { return (unsigned)((e >> 24) & 0x3); }
+inline int tmpl_pack(int ox, int oy, int oz, unsigned cls)
+{
+    return (int)((unsigned)(ox & 0xFF) | ((unsigned)(oy & 0xFF) << 8) | ((unsigned)(oz & 0xFF) << 16) |
+                 (cls << 24));
+}
+
+// ---- particle records ----------------------------------------------------------------------
+// What the sweep needs of each particle (read-only there; written by the particle phase).
+struct __align__(16) PKern {
+    double u[3];   // translational velocity u_p
+    double om[3];  // angular velocity omega_p
+    double phi[3]; // x_p0 - floor(x_p0): lever arm of offset o is o - phi
+    int K[3];      // anchor floor(x_p0) + shift: site of offset o is K + o
+    int pad;
+};
+
+// Constants of each particle.
+struct __align__(16) PConst {
+    double x0[3];  // centre when added
+    double r, inv_m, inv_I;
+    double ext[3]; // external velocity increment per step (buoyant gravity, body force)
+    int A[3];      // floor(x0)
+    int tmpl_off;  // first template entry
+    int tmpl_n;    // number of template entries
+    int pad;
+};
+
+// Device status word values (mirrors lbm_status codes).
+constexpr int ERR_CAPACITY = 8;
+constexpr int ERR_UNSTABLE = 9;
+
+// Per-step work-list sizes, cleared at the start of every particle phase.
+struct Counters {
+    int npairs;
+    int nchanged;
+    int nrestamp;
+    int pad;
+};
+
+struct Geom {
+    int nx, ny, nz;
+    int wall[3];     // 1 = halfway bounce-back walls on both ends of the axis
+    unsigned N;      // number of sites
+};
+
+// Everything the sweep and the getters read of the particle side.
+struct PartView {
+    const unsigned* tag;  // owner map [N] (nullptr when there are no particles)
+    const PKern* pk;      // [np]
+    const int* pending;   // 1: the IS imposition of the previous step is still to apply
+};
+
+__device__ inline int wrap_offset(int o, int n, bool periodic)
+{
+    if (!periodic) return o;
+    o %= n;
+    const int h = n / 2;
+    if (o < -h) o += n;
+    else if (o >= n - h) o -= n;
+    return o;
+}
+
+// Site index of offset o of a particle anchored at K; false when it lies beyond a wall.
+__device__ __forceinline__ bool site_of(const Geom& g, const int K[3], int ox, int oy, int oz,
+                                        unsigned& idx)
+{
+    int v[3] = {K[0] + ox, K[1] + oy, K[2] + oz};
+    const int n[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (g.wall[k]) {
+            if (v[k] < 0 || v[k] >= n[k]) return false;
+        } else {
+            v[k] %= n[k];
+            if (v[k] < 0) v[k] += n[k];
+        }
+    }
+    idx = ((unsigned)v[2] * (unsigned)g.ny + (unsigned)v[1]) * (unsigned)g.nx + (unsigned)v[0];
+    return true;
+}
+
+}  // namespace lbmp

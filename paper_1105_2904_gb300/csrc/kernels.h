@@ -1,0 +1,128 @@
+// Host-side interface between the translation units of the CUDA path: argument records
+// and launch functions. The sweep family is compiled once per storage format (double in
+// a TU built with -fmad=false so that it evaluates the same IEEE operations as a plain
+// FP64 implementation; float / half / bfloat16 in another).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace lbmp {
+
+struct SweepArgs {
+    int lattice;               // 0 = D2Q9, 1 = D3Q19
+    Geom g;
+    const void* fin;           // [Q][N] storage format
+    void* fout;                // [Q][N]
+    PartView pv;               // tag == nullptr: no particles
+    const void* stash_in;      // [N] compute type (double / float): site density (deviation)
+    void* stash_out;           // [N]
+    double* acc;               // [np][6] dP, dL accumulators (FP32 storage modes)
+    double* bs_scratch;        // [N][6] per-site dP, dL (FP64 mode, fixed-order reduction)
+    double omega, pre, F[3];   // 1/tau, 1 - 1/(2 tau), body force
+};
+
+struct MaterializeArgs {
+    int lattice;
+    Geom g;
+    const void* fin;
+    PartView pv;
+    const void* stash_in;
+    double F[3];
+    unsigned s0, count;        // site range [s0, s0 + count)
+    int mode;                  // 0: rho[count], u[count][3]; 1: f[Q][count]
+    double* out0;
+    double* out1;
+};
+
+struct ConvertArgs {
+    int lattice;
+    Geom g;
+    const double* f;           // [Q][count] plain distributions
+    void* dst;                 // [Q][N] storage format, unshifted
+    unsigned s0, count;
+};
+
+struct UnstreamArgs {
+    int lattice;
+    Geom g;
+    const void* src;           // [Q][N] storage format holding f at unshifted sites
+    void* dst;                 // [Q][N] pull-source layout
+};
+
+struct StashFixArgs {
+    int lattice;
+    Geom g;
+    const void* fout;          // [Q][N] buffer just written by the sweep
+    void* stash_out;           // [N]
+    const PKern* pk;
+    const PConst* pc;
+    const int* tmpl;
+    const int* list;           // particles whose shift changed
+    const Counters* cnt;       // cnt->nchanged entries of list
+};
+
+struct KernelTable {
+    void (*sweep)(const SweepArgs&, cudaStream_t);
+    void (*materialize)(const MaterializeArgs&, cudaStream_t);
+    void (*convert_in)(const ConvertArgs&, cudaStream_t);
+    void (*unstream)(const UnstreamArgs&, cudaStream_t);
+    void (*fill_rest)(int lattice, void* dst, unsigned N, cudaStream_t);
+    void (*stash_fix)(const StashFixArgs&, cudaStream_t);
+    int elem_bytes;
+    int compute_bytes;
+};
+
+const KernelTable* kernels_f64();
+const KernelTable* kernels_f32();
+const KernelTable* kernels_f16();
+const KernelTable* kernels_bf16();
+
+// ---- particle phase (particles.cu, FP64, -fmad=false) ---------------------------------------
+struct CellGrid {
+    int n[3];          // cells per axis
+    double size[3];    // cell edge per axis
+    int total;
+};
+
+struct ParticleArgs {
+    int lattice;
+    Geom g;
+    int np;
+    PKern* pk;
+    const PConst* pc;
+    const int* tmpl;
+    unsigned* tag;
+    double* x;          // [np][3] centres
+    int* Kold;          // [np][3] anchor before this step's move
+    double* un;         // [np][3] velocity during the contact step
+    double* acc;        // [np][6]
+    double* force;      // [np][6] -dP, -dL of the last step
+    const double* bs_scratch;  // FP64 mode: per-site dP, dL (nullptr otherwise)
+    Counters* cnt;
+    int* status;        // device status word (first fault wins)
+    int* pending;
+    CellGrid cg;
+    int* cell_of;       // [np]
+    int* cell_count;    // [total]
+    int* cell_start;    // [total + 1]
+    int* cell_cursor;   // [total]
+    int* cell_items;    // [np]
+    unsigned long long* pairs;  // [pair_cap]
+    int pair_cap;
+    int* changed;       // [np]
+    int* restamp;       // [np]
+    int* restamp_flag;  // [np]
+    double gap;
+};
+
+// Enqueues the particle phase of one step after the sweep: reduction (FP64 mode),
+// acceleration, contacts, move, re-marking. Returns the number of kernels launched.
+int launch_particle_phase(const ParticleArgs& a, cudaStream_t s);
+// Stamps every particle's site set into a cleared owner map (after lbm_add_particles).
+void launch_stamp_all(const ParticleArgs& a, cudaStream_t s);
+// Opts the contact kernel into the shared memory its pair list needs.
+cudaError_t prepare_particle_kernels(int pair_cap);
+
+}  // namespace lbmp

@@ -1,0 +1,408 @@
+// Particle phase of one step, FP64 throughout (built with -fmad=false so that the
+// arithmetic is evaluated exactly as written):
+//   reduction of the exchanged momentum in a fixed order (FP64 storage mode only),
+//   acceleration (Eqs. 10-11), hard-core contacts (Sec. 2.3, Eqs. 16-19; predicted-overlap
+//   trigger, pairs processed in (i, j) order), position update (Eq. 13) and the integer
+//   shift of each site set (Eqs. 14-15), then the incremental re-marking of the owner map
+//   for the particles whose shift changed and their neighbours.
+#include "kernels.h"
+
+namespace lbmp {
+
+namespace {
+
+constexpr int PT = 128;  // threads per block of the per-particle kernels
+
+__device__ inline void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+__device__ inline double min_image(double d, int n, bool periodic)
+{
+    if (!periodic) return d;
+    return d - (double)n * floor(d / (double)n + 0.5);
+}
+
+__device__ inline int axis_len(const Geom& g, int k) { return k == 0 ? g.nx : (k == 1 ? g.ny : g.nz); }
+
+__device__ inline bool periodic_axis(const Geom& g, int k, int D) { return k < D && !g.wall[k]; }
+
+// Fixed-order sum of the per-site momentum exchange of each particle: template order
+// (z, y, x lexicographic offsets), only sites the particle owns as BS (Eqs. 8-9).
+__global__ void k_reduce_ordered(const ParticleArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const PConst pc = a.pc[p];
+    int K[3] = {a.pk[p].K[0], a.pk[p].K[1], a.pk[p].K[2]};
+    const unsigned code = (CLS_BS << 30) | (unsigned)p;
+    double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int e = 0; e < pc.tmpl_n; ++e) {
+        const int ent = a.tmpl[pc.tmpl_off + e];
+        if (tmpl_cls(ent) != CLS_BS) continue;
+        unsigned site;
+        if (!site_of(a.g, K, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+        if (a.tag[site] != code) continue;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s[q] += a.bs_scratch[(size_t)site * 6 + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) a.acc[(size_t)p * 6 + q] = s[q];
+}
+
+__device__ inline int cell_coord(const ParticleArgs& a, int k, double x)
+{
+    const int n = axis_len(a.g, k);
+    const int D = a.lattice == 0 ? 2 : 3;
+    if (k >= D) return 0;
+    double v;
+    if (a.g.wall[k]) {
+        v = x + 0.5;
+    } else {
+        v = x - (double)n * floor(x / (double)n);
+    }
+    int c = (int)floor(v / a.cg.size[k]);
+    if (c < 0) c = 0;
+    if (c >= a.cg.n[k]) c = a.cg.n[k] - 1;
+    return c;
+}
+
+// Eqs. 10-11 (+ external increment), force/torque output, cell of the current centre.
+__global__ void k_accel(const ParticleArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const PConst pc = a.pc[p];
+    PKern& k = a.pk[p];
+    double d[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        d[q] = a.acc[(size_t)p * 6 + q];
+        a.acc[(size_t)p * 6 + q] = 0.0;
+        a.force[(size_t)p * 6 + q] = -d[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        a.un[(size_t)p * 3 + q] = (k.u[q] - d[q] * pc.inv_m) + pc.ext[q];
+        k.om[q] = k.om[q] - d[3 + q] * pc.inv_I;
+    }
+    const int c0 = cell_coord(a, 0, a.x[(size_t)p * 3 + 0]);
+    const int c1 = cell_coord(a, 1, a.x[(size_t)p * 3 + 1]);
+    const int c2 = cell_coord(a, 2, a.x[(size_t)p * 3 + 2]);
+    const int c = (c2 * a.cg.n[1] + c1) * a.cg.n[0] + c0;
+    a.cell_of[p] = c;
+    atomicAdd(&a.cell_count[c], 1);
+}
+
+// Exclusive scan of the cell counts (one block).
+__global__ void k_cell_scan(const ParticleArgs a)
+{
+    __shared__ int part[1024];
+    const int n = a.cg.total;
+    const int T = blockDim.x;
+    const int chunk = (n + T - 1) / T;
+    const int b = threadIdx.x * chunk;
+    const int e = min(n, b + chunk);
+    int s = 0;
+    for (int i = b; i < e; ++i) s += a.cell_count[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - s;
+    for (int i = b; i < e; ++i) {
+        a.cell_start[i] = run;
+        run += a.cell_count[i];
+    }
+    if (threadIdx.x == T - 1) a.cell_start[n] = part[T - 1];
+}
+
+__global__ void k_cell_fill(const ParticleArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const int c = a.cell_of[p];
+    a.cell_items[a.cell_start[c] + atomicAdd(&a.cell_cursor[c], 1)] = p;
+}
+
+// Distinct neighbouring cell coordinates along one axis (1 to 3 of them).
+__device__ inline int nbr_cells(const ParticleArgs& a, int k, int c, int out[3])
+{
+    const int n = a.cg.n[k];
+    if (n == 1) { out[0] = 0; return 1; }
+    if (n == 2) { out[0] = 0; out[1] = 1; return 2; }
+    int m = 0;
+    for (int d = -1; d <= 1; ++d) {
+        int v = c + d;
+        if (v < 0 || v >= n) {
+            if (a.g.wall[k]) continue;
+            v = (v + n) % n;
+        }
+        out[m++] = v;
+    }
+    return m;
+}
+
+// Candidate pairs (i < j) whose predicted centres overlap: |(x_i+u_i')-(x_j+u_j')| < r_i+r_j+gap.
+__global__ void k_pairs(const ParticleArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.np) return;
+    const int D = a.lattice == 0 ? 2 : 3;
+    const int c = a.cell_of[i];
+    const int cc[3] = {c % a.cg.n[0], (c / a.cg.n[0]) % a.cg.n[1], c / (a.cg.n[0] * a.cg.n[1])};
+    int lx[3], ly[3], lz[3];
+    const int nxc = nbr_cells(a, 0, cc[0], lx), nyc = nbr_cells(a, 1, cc[1], ly),
+              nzc = nbr_cells(a, 2, cc[2], lz);
+    const double ri = a.pc[i].r;
+    double xi[3], ui[3];
+    for (int k = 0; k < 3; ++k) {
+        xi[k] = a.x[(size_t)i * 3 + k];
+        ui[k] = a.un[(size_t)i * 3 + k];
+    }
+    for (int zz = 0; zz < nzc; ++zz)
+        for (int yy = 0; yy < nyc; ++yy)
+            for (int xx = 0; xx < nxc; ++xx) {
+                const int cell = (lz[zz] * a.cg.n[1] + ly[yy]) * a.cg.n[0] + lx[xx];
+                for (int s = a.cell_start[cell]; s < a.cell_start[cell + 1]; ++s) {
+                    const int j = a.cell_items[s];
+                    if (j <= i) continue;
+                    double d2 = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        double pd = (a.x[(size_t)j * 3 + k] + a.un[(size_t)j * 3 + k]) - (xi[k] + ui[k]);
+                        pd = min_image(pd, axis_len(a.g, k), periodic_axis(a.g, k, D));
+                        d2 += pd * pd;
+                    }
+                    const double R = ri + a.pc[j].r + a.gap;
+                    if (d2 < R * R) {
+                        const int slot = atomicAdd(&a.cnt->npairs, 1);
+                        if (slot < a.pair_cap)
+                            a.pairs[slot] = ((unsigned long long)i << 32) | (unsigned long long)j;
+                        else
+                            set_status(a.status, ERR_CAPACITY);
+                    }
+                }
+            }
+}
+
+// One block: sort the candidate pairs, resolve them serially in (i, j) order, then the
+// walls, the position update, the new shifts and the list of particles whose shift changed.
+__global__ void k_resolve_move(const ParticleArgs a)
+{
+    extern __shared__ unsigned long long keys[];
+    const int D = a.lattice == 0 ? 2 : 3;
+    const int T = blockDim.x;
+    int n = a.cnt->npairs;
+    if (n > a.pair_cap) n = 0;  // over capacity: status already set, contacts skipped
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int t = threadIdx.x; t < m; t += T) keys[t] = t < n ? a.pairs[t] : ~0ull;
+    __syncthreads();
+    // bitonic sort of m keys
+    for (int size = 2; size <= m; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < m; t += T) {
+                const int u = t ^ stride;
+                if (u > t) {
+                    const bool up = (t & size) == 0;
+                    const unsigned long long A = keys[t], B = keys[u];
+                    if ((A > B) == up) {
+                        keys[t] = B;
+                        keys[u] = A;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < n; ++q) {
+            const int i = (int)(keys[q] >> 32), j = (int)(keys[q] & 0xffffffffu);
+            const double ai = a.pc[i].inv_m, aj = a.pc[j].inv_m;
+            const double den = ai + aj;
+            if (den == 0.0) continue;
+            double d[3], nn[3];
+            for (int k = 0; k < 3; ++k)
+                d[k] = min_image(a.x[(size_t)j * 3 + k] - a.x[(size_t)i * 3 + k], axis_len(a.g, k),
+                                 periodic_axis(a.g, k, D));
+            const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (dn == 0.0) continue;
+            for (int k = 0; k < 3; ++k) nn[k] = d[k] / dn;
+            double* ui = &a.un[(size_t)i * 3];
+            double* uj = &a.un[(size_t)j * 3];
+            const double w = (uj[0] - ui[0]) * nn[0] + (uj[1] - ui[1]) * nn[1] + (uj[2] - ui[2]) * nn[2];
+            if (!(w < 0.0)) continue;
+            const double ci = 2.0 * ai * w / den;
+            const double cj = 2.0 * aj * w / den;
+            for (int k = 0; k < 3; ++k) {
+                ui[k] = ui[k] + ci * nn[k];
+                uj[k] = uj[k] - cj * nn[k];
+            }
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < a.np; p += T) {
+        const PConst pc = a.pc[p];
+        double* u = &a.un[(size_t)p * 3];
+        double* x = &a.x[(size_t)p * 3];
+        if (pc.inv_m != 0.0) {
+            const double R = pc.r + a.gap;
+            for (int k = 0; k < D; ++k) {
+                if (!a.g.wall[k]) continue;
+                const double xp = x[k] + u[k];
+                const double lo = xp + 0.5;
+                const double hi = ((double)axis_len(a.g, k) - 0.5) - xp;
+                if (lo < R && u[k] < 0.0)
+                    u[k] = -u[k];
+                else if (hi < R && u[k] > 0.0)
+                    u[k] = -u[k];
+            }
+        }
+        PKern& k = a.pk[p];
+        bool changed = false;
+        for (int q = 0; q < 3; ++q) k.u[q] = u[q];
+        for (int q = 0; q < 3; ++q) a.Kold[(size_t)p * 3 + q] = k.K[q];
+        for (int q = 0; q < D; ++q) {
+            x[q] = x[q] + u[q];
+            const int s = (int)floor((x[q] - pc.x0[q]) + 0.5);
+            const int Kn = pc.A[q] + s;
+            const int dK = Kn - k.K[q];
+            if (dK != 0) changed = true;
+            if (dK > 1 || dK < -1) set_status(a.status, ERR_UNSTABLE);
+            k.K[q] = Kn;
+        }
+        if (changed) a.changed[atomicAdd(&a.cnt->nchanged, 1)] = p;
+    }
+    if (threadIdx.x == 0) *a.pending = 1;
+}
+
+__device__ inline void add_restamp(const ParticleArgs& a, int q)
+{
+    if (atomicExch(&a.restamp_flag[q], 1) == 0) a.restamp[atomicAdd(&a.cnt->nrestamp, 1)] = q;
+}
+
+// Particles whose site sets may meet the old or new set of a moved particle.
+__global__ void k_mark_neighbours(const ParticleArgs a)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.cnt->nchanged) return;
+    const int D = a.lattice == 0 ? 2 : 3;
+    const int p = a.changed[t];
+    add_restamp(a, p);
+    const int c = a.cell_of[p];
+    const int cc[3] = {c % a.cg.n[0], (c / a.cg.n[0]) % a.cg.n[1], c / (a.cg.n[0] * a.cg.n[1])};
+    int lx[3], ly[3], lz[3];
+    const int nxc = nbr_cells(a, 0, cc[0], lx), nyc = nbr_cells(a, 1, cc[1], ly),
+              nzc = nbr_cells(a, 2, cc[2], lz);
+    const double rp = a.pc[p].r;
+    double cold[3], cnew[3];
+    for (int k = 0; k < 3; ++k) {
+        cold[k] = (double)a.Kold[(size_t)p * 3 + k] + a.pk[p].phi[k];
+        cnew[k] = (double)a.pk[p].K[k] + a.pk[p].phi[k];
+    }
+    for (int zz = 0; zz < nzc; ++zz)
+        for (int yy = 0; yy < nyc; ++yy)
+            for (int xx = 0; xx < nxc; ++xx) {
+                const int cell = (lz[zz] * a.cg.n[1] + ly[yy]) * a.cg.n[0] + lx[xx];
+                for (int s = a.cell_start[cell]; s < a.cell_start[cell + 1]; ++s) {
+                    const int q = a.cell_items[s];
+                    if (q == p) continue;
+                    const double R = rp + a.pc[q].r + 1.0;
+                    double d2o = 0.0, d2n = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        const double cq = (double)a.pk[q].K[k] + a.pk[q].phi[k];
+                        const double dd0 = min_image(cold[k] - cq, axis_len(a.g, k), periodic_axis(a.g, k, D));
+                        const double dd1 = min_image(cnew[k] - cq, axis_len(a.g, k), periodic_axis(a.g, k, D));
+                        d2o += dd0 * dd0;
+                        d2n += dd1 * dd1;
+                    }
+                    if (d2o <= R * R || d2n <= R * R) add_restamp(a, q);
+                }
+            }
+}
+
+// Releases the sites a moved particle owned at its old anchor.
+__global__ void k_mark_clear(const ParticleArgs a)
+{
+    const int nlist = a.cnt->nchanged;
+    for (int b = blockIdx.x; b < nlist; b += gridDim.x) {
+        const int p = a.changed[b];
+        const PConst pc = a.pc[p];
+        const int K[3] = {a.Kold[(size_t)p * 3], a.Kold[(size_t)p * 3 + 1], a.Kold[(size_t)p * 3 + 2]};
+        for (int e = threadIdx.x; e < pc.tmpl_n; e += blockDim.x) {
+            const int ent = a.tmpl[pc.tmpl_off + e];
+            unsigned site;
+            if (!site_of(a.g, K, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+            const unsigned t = a.tag[site];
+            if (t != TAG_FLUID && (t & PID_MASK) == (unsigned)p) a.tag[site] = TAG_FLUID;
+        }
+    }
+}
+
+// Claims the sites of a particle at its current anchor; the lowest code wins.
+__device__ inline void stamp_particle(const ParticleArgs& a, int p)
+{
+    const PConst pc = a.pc[p];
+    const int K[3] = {a.pk[p].K[0], a.pk[p].K[1], a.pk[p].K[2]};
+    for (int e = threadIdx.x; e < pc.tmpl_n; e += blockDim.x) {
+        const int ent = a.tmpl[pc.tmpl_off + e];
+        unsigned site;
+        if (!site_of(a.g, K, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+        atomicMin(&a.tag[site], (tmpl_cls(ent) << 30) | (unsigned)p);
+    }
+}
+
+__global__ void k_mark_stamp(const ParticleArgs a)
+{
+    const int nlist = a.cnt->nrestamp;
+    for (int b = blockIdx.x; b < nlist; b += gridDim.x) stamp_particle(a, a.restamp[b]);
+}
+
+__global__ void k_stamp_all(const ParticleArgs a)
+{
+    for (int b = blockIdx.x; b < a.np; b += gridDim.x) stamp_particle(a, b);
+}
+
+int mark_grid() { return 304; }
+
+}  // namespace
+
+int launch_particle_phase(const ParticleArgs& a, cudaStream_t s)
+{
+    const int blocks = (a.np + PT - 1) / PT;
+    int launches = 0;
+    cudaMemsetAsync(a.cnt, 0, sizeof(Counters), s);
+    cudaMemsetAsync(a.cell_count, 0, sizeof(int) * (size_t)a.cg.total, s);
+    cudaMemsetAsync(a.cell_cursor, 0, sizeof(int) * (size_t)a.cg.total, s);
+    cudaMemsetAsync(a.restamp_flag, 0, sizeof(int) * (size_t)a.np, s);
+    if (a.bs_scratch) {
+        k_reduce_ordered<<<blocks, PT, 0, s>>>(a);
+        ++launches;
+    }
+    k_accel<<<blocks, PT, 0, s>>>(a);
+    k_cell_scan<<<1, 1024, 0, s>>>(a);
+    k_cell_fill<<<blocks, PT, 0, s>>>(a);
+    k_pairs<<<blocks, PT, 0, s>>>(a);
+    const size_t smem = sizeof(unsigned long long) * (size_t)a.pair_cap;
+    k_resolve_move<<<1, 1024, smem, s>>>(a);
+    k_mark_neighbours<<<blocks, PT, 0, s>>>(a);
+    k_mark_clear<<<mark_grid(), 256, 0, s>>>(a);
+    k_mark_stamp<<<mark_grid(), 256, 0, s>>>(a);
+    launches += 8;
+    return launches;
+}
+
+void launch_stamp_all(const ParticleArgs& a, cudaStream_t s)
+{
+    k_stamp_all<<<mark_grid(), 256, 0, s>>>(a);
+}
+
+cudaError_t prepare_particle_kernels(int pair_cap)
+{
+    return cudaFuncSetAttribute(k_resolve_move, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(unsigned long long) * (size_t)pair_cap));
+}
+
+}  // namespace lbmp

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of the C-ABI in ``include/lbmp.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls. ``Simulation`` bundles a
+context handle with numpy-returning getters; it adds no arithmetic of its own. The
+library must have been built (``paper_1105_2904_gb300.build.build()``); loading fails
+loudly otherwise, and every call raises ``LbmError`` on a non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbmp.so")
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", 1: "LBM_E_INVALID", 2: "LBM_E_OOM", 3: "LBM_E_CUDA", 4: "LBM_E_OVERLAP",
+          5: "LBM_E_TIMEOUT", 6: "LBM_E_STATE", 7: "LBM_E_NAN", 8: "LBM_E_CAPACITY", 9: "LBM_E_UNSTABLE"}
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16DEV, "bf16": LBM_BF16DEV}
+LBM_PERIODIC, LBM_NOSLIP = 0, 1
+
+EXPORTED = ("lbm_create", "lbm_configure", "lbm_add_particles", "lbm_step", "lbm_synchronize",
+            "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
+            "lbm_get_masks", "lbm_get_info", "lbm_last_error", "lbm_destroy")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads liblbmp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("liblbmp.so not found at %s: build it with paper_1105_2904_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    I = ctypes.POINTER(ctypes.c_int)
+    i32 = ctypes.c_int
+    lib.lbm_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, i32, ctypes.c_double, D]
+    lib.lbm_configure.argtypes = [P, i32, I, D, ctypes.c_double, i32, P]
+    lib.lbm_add_particles.argtypes = [P, i32, D, D, D, D, D, I]
+    lib.lbm_step.argtypes = [P, i32]
+    lib.lbm_synchronize.argtypes = [P]
+    lib.lbm_get_fields.argtypes = [P, D, D]
+    lib.lbm_get_particles.argtypes = [P, D, D, D, D, D]
+    lib.lbm_get_distributions.argtypes = [P, D]
+    lib.lbm_set_distributions.argtypes = [P, D]
+    lib.lbm_get_masks.argtypes = [P, ctypes.POINTER(ctypes.c_uint)]
+    lib.lbm_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbm_last_error.argtypes = [P]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_destroy.argtypes = [P]
+    for name in EXPORTED:
+        if name not in ("lbm_last_error", "lbm_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    lib.lbm_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, n=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if n is None else a.reshape(n)
+
+
+def _check(h, status):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(h) if h else b"(no context)"
+        raise LbmError(status, msg.decode(errors="replace") if msg else "")
+
+
+# ---- same-name wrappers ------------------------------------------------------------------
+
+def lbm_create(lattice, nx, ny, nz, tau, body_force=None):
+    lib = load()
+    h = ctypes.c_void_p()
+    F = _f64(body_force, 3)
+    st = lib.lbm_create(ctypes.byref(h), int(lattice), int(nx), int(ny), int(nz), float(tau), _dp(F))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_create(%d, %d, %d, %d, %g)" % (lattice, nx, ny, nz, tau))
+    return h
+
+
+def lbm_configure(h, precision, faces=None, particle_gravity=None, contact_gap=0.0,
+                  body_force_on_particles=False, cuda_stream=None):
+    lib = load()
+    fa = None if faces is None else np.ascontiguousarray(faces, dtype=np.int32).reshape(6)
+    g = _f64(particle_gravity, 3)
+    _check(h, lib.lbm_configure(h, int(precision),
+                                None if fa is None else fa.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                _dp(g), float(contact_gap), int(bool(body_force_on_particles)),
+                                ctypes.c_void_p(cuda_stream) if cuda_stream else None))
+
+
+def lbm_add_particles(h, centers, radii, densities, velocities=None, omegas=None):
+    lib = load()
+    c = _f64(centers).reshape(-1, 3)
+    n = c.shape[0]
+    r = _f64(radii, n)
+    d = _f64(densities, n)
+    v = None if velocities is None else _f64(velocities).reshape(n, 3)
+    o = None if omegas is None else _f64(omegas).reshape(n, 3)
+    first = ctypes.c_int(-1)
+    _check(h, lib.lbm_add_particles(h, n, _dp(c), _dp(r), _dp(d), _dp(v), _dp(o), ctypes.byref(first)))
+    return first.value
+
+
+def lbm_step(h, n=1):
+    _check(h, load().lbm_step(h, int(n)))
+
+
+def lbm_synchronize(h):
+    _check(h, load().lbm_synchronize(h))
+
+
+def lbm_get_fields(h, N, rho=None, u=None):
+    rho = np.empty(N) if rho is None else rho
+    u = np.empty((N, 3)) if u is None else u
+    _check(h, load().lbm_get_fields(h, _dp(rho), _dp(u)))
+    return rho, u
+
+
+def lbm_get_particles(h, n, out=None):
+    out = out or {k: np.empty((n, 3)) for k in ("x", "u", "omega", "force", "torque")}
+    _check(h, load().lbm_get_particles(h, _dp(out["x"]), _dp(out["u"]), _dp(out["omega"]),
+                                       _dp(out["force"]), _dp(out["torque"])))
+    return out
+
+
+def lbm_get_distributions(h, Q, N, f=None):
+    f = np.empty((Q, N)) if f is None else f
+    _check(h, load().lbm_get_distributions(h, _dp(f)))
+    return f
+
+
+def lbm_set_distributions(h, f):
+    f = _f64(f)
+    _check(h, load().lbm_set_distributions(h, _dp(f)))
+
+
+def lbm_get_masks(h, N):
+    t = np.empty(N, dtype=np.uint32)
+    _check(h, load().lbm_get_masks(h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint))))
+    return t
+
+
+def lbm_get_info(h):
+    out = (ctypes.c_longlong * 6)()
+    _check(h, load().lbm_get_info(h, out))
+    keys = ("particles", "steps", "launches_per_step", "device_bytes", "bytes_per_site", "precision")
+    return dict(zip(keys, list(out)))
+
+
+def lbm_last_error(h):
+    m = load().lbm_last_error(h)
+    return m.decode(errors="replace") if m else ""
+
+
+def lbm_destroy(h):
+    if h:
+        load().lbm_destroy(h)
+
+
+class Simulation:
+    """A context handle plus numpy-shaped getters (lattice 0 = D2Q9, 1 = D3Q19)."""
+
+    def __init__(self, lattice, nx, ny, nz, tau, body_force=(0.0, 0.0, 0.0), precision="fp32",
+                 walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False,
+                 cuda_stream=None):
+        self.lattice = lattice
+        self.Q = 9 if lattice == LBM_D2Q9 else 19
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.h = lbm_create(lattice, nx, ny, nz, tau, body_force)
+        faces = [LBM_NOSLIP if walls[k // 2] else LBM_PERIODIC for k in range(6)]
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        try:
+            lbm_configure(self.h, prec, faces, gravity, gap, body_force_on_particles, cuda_stream)
+        except Exception:
+            lbm_destroy(self.h)
+            self.h = None
+            raise
+        self.np = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def add_particles(self, centers, radii, densities, velocities=None, omegas=None):
+        first = lbm_add_particles(self.h, centers, radii, densities, velocities, omegas)
+        self.np = lbm_get_info(self.h)["particles"]
+        return first
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def synchronize(self):
+        lbm_synchronize(self.h)
+
+    def get_fields(self):
+        rho, u = lbm_get_fields(self.h, self.N)
+        return rho.reshape(self.shape), u.reshape(self.shape + (3,))
+
+    def get_particles(self):
+        return lbm_get_particles(self.h, self.np)
+
+    def get_f(self):
+        return lbm_get_distributions(self.h, self.Q, self.N).reshape((self.Q,) + self.shape)
+
+    def set_f(self, f):
+        lbm_set_distributions(self.h, np.ascontiguousarray(f, dtype=np.float64).reshape(self.Q, self.N))
+
+    def get_tags(self):
+        return lbm_get_masks(self.h, self.N).reshape(self.shape)
+
+    def info(self):
+        return lbm_get_info(self.h)
