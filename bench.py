@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of one suspension time step (MLUPS and HBM roofline fraction).
+
+Default workload: D3Q19, 512^3 periodic box, 16000 spheres of radius 8 (25.6 % solid) at
+seeded random positions, velocities N(0, 1e-3), density ratio 1.2, tau 0.6, body force
+1e-6, FP32 arithmetic on FP32 deviation storage. A "step" is one full time step of the
+method: fused stream + collide + boundary-site transfer over all sites, the per-particle
+reduction, particle update and contacts, re-marking, and the internal-site imposition.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (the path is not
+decomposed across GPUs); value = sites x steps x ranks / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1105_2904_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MLUPS"
+UNIT = "MLUPS"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="d3q19_512", choices=["d3q19_512", "d2q9_sedimentation"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
+    p.add_argument("--edge", type=int, default=0, help="override the 3D box edge (same solid fraction)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(args):
+    if args.workload == "d2q9_sedimentation":
+        return W.sedimentation_2d()
+    if args.edge:
+        return W.suspension_3d_scaled(args.edge)
+    return W.suspension_3d()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in ("sweep.cuh", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1105_2904_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel_key):
+    """ncu DRAM bytes per site of the sweep kernel, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    rec = d.get(kernel_key)
+    if not rec or rec.get("source_sha") != source_sha():
+        return None
+    return rec
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(wl, target_s=12.0):
+    """The FP64 oracle, as it stands (one host thread), on a bounded sample of the workload:
+    the same suspension scaled to a smaller periodic box with the same solid fraction."""
+    import oracle as O
+
+    edge = 64 if wl.lattice == "D3Q19" else 256
+    if wl.lattice == "D3Q19":
+        s = W.suspension_3d_scaled(edge)
+        c, r, d, v = s.particles()
+        sim = O.OracleSim(O.D3Q19, edge, edge, edge, s.tau, body_force=s.body_force,
+                          body_force_on_particles=s.body_force_on_particles)
+        sample = "D3Q19 %d^3 periodic, %d spheres r=8 (same solid fraction)" % (edge, len(r))
+    else:
+        s = wl
+        n = max(1, int(round(wl.n_particles * (edge * edge * 2) / wl.sites)))
+        c, r = W.rsa_centers((edge, 2 * edge), n, wl.radius, seed=wl.seed, min_gap=wl.min_gap, walls=wl.walls)
+        d = np.full(n, wl.density_ratio)
+        v = None
+        sim = O.OracleSim(O.D2Q9, edge, 2 * edge, 1, wl.tau, walls=wl.walls, gravity=wl.gravity,
+                          gap=0.0)
+        sample = "D2Q9 %dx%d closed box, %d disks r=10" % (edge, 2 * edge, n)
+    sim.add_particles(c, r, d, v)
+    sites = sim.N
+    t = time.perf_counter()
+    sim.step(1)
+    one = time.perf_counter() - t
+    steps = max(1, int(target_s / max(one, 1e-6)))
+    t = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t
+    return {"value": sites * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%s, %d steps, %.1f s, single-threaded FP64 C" % (sample, steps, dt)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+
+    wl = workload(args)
+    t0 = time.perf_counter()
+    # calibrate the per-site cost, then size the sample so that the run ends in ~1-2 minutes
+    s32 = W.suspension_3d_scaled(32)
+    c, r, d, v = s32.particles()
+    cal = O.OracleSim(O.D3Q19, 32, 32, 32, s32.tau, body_force=s32.body_force, body_force_on_particles=True)
+    cal.add_particles(c, r, d, v)
+    t = time.perf_counter()
+    cal.step(2)
+    per_site = (time.perf_counter() - t) / (2 * 32 ** 3)
+    budget = 90.0 / max(1, args.steps + args.warmup)
+    edge = int(max(24, min(128, (budget / per_site) ** (1.0 / 3.0))))
+    s = W.suspension_3d_scaled(edge)
+    c, r, d, v = s.particles()
+    sim = O.OracleSim(O.D3Q19, edge, edge, edge, s.tau, body_force=s.body_force, body_force_on_particles=True)
+    sim.add_particles(c, r, d, v)
+    sim.step(args.warmup)
+    t = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t
+    value = sim.N * args.steps / dt / 1e6
+    sample = ("D3Q19 %d^3 periodic, %d spheres r=8 (the %s workload scaled to the same solid fraction), "
+              "FP64 oracle, single-threaded" % (edge, len(r), wl.name))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "sample_edge": edge},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1105_2904_gb300 import build as B
+    from paper_1105_2904_gb300 import lbmp
+
+    B.build()
+    wl = workload(args)
+    lattice = 1 if wl.lattice == "D3Q19" else 0
+    nx, ny, nz = wl.dims
+    N = wl.sites
+    c, r, d, v = wl.particles()
+    # A dedicated stream (torch's default stream has handle 0): the library enqueues all
+    # of its work on it and the timing events are recorded on it.
+    stream = torch.cuda.Stream()
+
+    def make():
+        sim = lbmp.Simulation(lattice, nx, ny, nz, wl.tau, body_force=wl.body_force, precision=args.precision,
+                              walls=wl.walls, gravity=wl.gravity, gap=0.0,
+                              body_force_on_particles=wl.body_force_on_particles, cuda_stream=stream.cuda_stream)
+        sim.add_particles(c, r, d, v)
+        return sim
+
+    sim = make()
+    sim.step(args.warmup)
+    sim.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    sim.synchronize()   # raises on a device fault recorded during the timed steps
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    info = sim.info()
+    value = N * args.steps * world / (ms / 1e3) / 1e6
+
+    # Roofline of the dominant kernel (the sweep): per-launch duration with CUDA events.
+    prof = sim.profile(min(args.steps, 50))
+    bytes_per_site = info["bytes_per_site"]
+    algo_bytes = bytes_per_site * N
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / (prof["sweep_ms"] / 1e3) / 1e9
+    kernel_key = "sweep_%s_%s" % (wl.lattice.lower(), args.precision)
+    rec = traffic_record(kernel_key)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (rec["dram_bytes_per_site"] * N if rec else None),
+                "kernel": "k_sweep (fused pull-stream + collide + BS transfer)",
+                "algorithmic_bytes_per_launch": algo_bytes, "sweep_ms": prof["sweep_ms"],
+                "particle_phase_ms": prof["particle_ms"], "step_ms_ungraphed": prof["step_ms"],
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"}
+    del sim
+    torch.cuda.synchronize()
+
+    # End to end through the C-ABI with host buffers: create, configure, upload particles,
+    # then every step enqueue it and read the particle state (positions, velocities, forces)
+    # back to host arrays.
+    e2e = None
+    if not args.no_e2e:
+        n = len(r)
+        host = {k: np.empty((n, 3)) for k in ("x", "u", "omega", "force", "torque")}
+        torch.cuda.synchronize()
+        barrier()
+        t = time.perf_counter()
+        s2 = make()
+        for _ in range(args.steps):
+            s2.step(1)
+            lbmp.lbm_get_particles(s2.h, n, host)
+        dt = time.perf_counter() - t
+        s2.close()
+        if world > 1:
+            tt = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            dt = float(tt.item())
+        h2d = (c.nbytes + r.nbytes + d.nbytes + v.nbytes) / args.steps
+        e2e = {"value": N * args.steps * world / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(5 * n * 3 * 8),
+               "includes": "context creation, particle upload and site classification, %d steps each "
+                           "followed by a particle-state read-back" % args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        solid = len(r) * (4.0 / 3.0 * math.pi * wl.radius ** 3) / N if lattice == 1 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "lattice": wl.lattice, "dims": list(wl.dims),
+                       "particles": len(r), "radius": wl.radius, "solid_fraction": solid, "tau": wl.tau,
+                       "storage": {"fp32": "fp32 deviations", "fp16": "fp16 scaled deviations",
+                                   "bf16": "bf16 scaled deviations", "fp64": "fp64"}[args.precision],
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: %.1f GB of distributions per step"
+                             % (bytes_per_site * N / 1e9)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(info["launches_per_step"]) * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -144,6 +144,14 @@ lbm_status lbm_get_masks(lbm_ctx* ctx, unsigned* tags);
  * (2 Q b), out[5] = precision. Returns LBM_E_INVALID if out is NULL. */
 lbm_status lbm_get_info(lbm_ctx* ctx, long long out[6]);
 
+/* Runs n steps like lbm_step but without graph capture, timing kernel groups with CUDA
+ * events on the context's stream: out_ms[0] = mean duration of the main sweep kernel (the
+ * fused propagation + collision + boundary-site transfer over every site), out_ms[1] =
+ * mean duration of the particle phase (its kernels back to back, launch gaps included),
+ * out_ms[2] = mean duration of a whole step. Advances the simulation by n steps and
+ * synchronizes. Errors as lbm_step; LBM_E_INVALID if n < 1 or out_ms is NULL. */
+lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3]);
+
 /* Description of the last non-OK status of ctx (static storage; never NULL). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

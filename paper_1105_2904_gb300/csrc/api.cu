@@ -38,15 +38,18 @@ struct lbm_ctx {
     void* f[2] = {nullptr, nullptr};
     void* stash[2] = {nullptr, nullptr};
     unsigned* tag = nullptr;
-    double* bs_scratch = nullptr;
+    unsigned* ismask = nullptr;
+    void* bs_scratch = nullptr;
     int cur = 0;
 
     int np = 0;
     std::vector<PConst> h_pc;
     std::vector<PKern> h_pk;
+    std::vector<PKernF> h_pkf;
     std::vector<double> h_x;
     std::vector<int> h_tmpl;
     PKern* pk = nullptr;
+    PKernF* pkf = nullptr;
     PConst* pc = nullptr;
     int* tmpl = nullptr;
     double *x = nullptr, *un = nullptr, *acc = nullptr, *force = nullptr;
@@ -215,6 +218,7 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     a.g = ctx->g;
     a.np = ctx->np;
     a.pk = ctx->pk;
+    a.pkf = ctx->pkf;
     a.pc = ctx->pc;
     a.tmpl = ctx->tmpl;
     a.tag = ctx->tag;
@@ -224,6 +228,7 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     a.acc = ctx->acc;
     a.force = ctx->force;
     a.bs_scratch = ctx->bs_scratch;
+    a.scratch_f64 = ctx->precision == LBM_FP64;
     a.cnt = ctx->cnt;
     a.status = ctx->status;
     a.pending = ctx->pending;
@@ -242,17 +247,36 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     return a;
 }
 
+MaskArgs mask_args(lbm_ctx* ctx, bool restamp_list)
+{
+    MaskArgs m{};
+    m.lattice = ctx->lattice;
+    m.g = ctx->g;
+    m.tag = ctx->tag;
+    m.ismask = ctx->ismask;
+    m.pk = ctx->pk;
+    m.pc = ctx->pc;
+    m.tmpl = ctx->tmpl;
+    m.list = restamp_list ? ctx->restamp : nullptr;
+    m.cnt = ctx->cnt;
+    m.np = ctx->np;
+    return m;
+}
+
 PartView part_view(lbm_ctx* ctx)
 {
     PartView v{};
     v.tag = ctx->np > 0 ? ctx->tag : nullptr;
     v.pk = ctx->pk;
+    v.pkf = ctx->pkf;
     v.pending = ctx->pending;
+    v.ismask = ctx->ismask;
     return v;
 }
 
-// One time step on ctx->stream, reading buffer c and writing buffer 1 - c.
-int enqueue_step(lbm_ctx* ctx, int c)
+// One time step on ctx->stream, reading buffer c and writing buffer 1 - c. With ev != nullptr
+// CUDA events are recorded before the sweep, after it, and after the particle phase.
+int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
 {
     SweepArgs a{};
     a.lattice = ctx->lattice;
@@ -262,12 +286,16 @@ int enqueue_step(lbm_ctx* ctx, int c)
     a.pv = part_view(ctx);
     a.stash_in = ctx->stash[c];
     a.stash_out = ctx->stash[1 - c];
-    a.acc = ctx->acc;
     a.bs_scratch = ctx->bs_scratch;
     a.omega = 1.0 / ctx->tau;
     a.pre = 1.0 - 0.5 / ctx->tau;
     for (int k = 0; k < 3; ++k) a.F[k] = ctx->F[k];
+    a.omega_f = (float)a.omega;
+    a.pre_f = (float)a.pre;
+    for (int k = 0; k < 3; ++k) a.F_f[k] = (float)ctx->F[k];
+    if (ev) cudaEventRecord(ev[0], ctx->stream);
     ctx->kt->sweep(a, ctx->stream);
+    if (ev) cudaEventRecord(ev[1], ctx->stream);
     int launches = 1;
     if (ctx->np > 0) {
         launches += launch_particle_phase(particle_args(ctx), ctx->stream);
@@ -282,8 +310,10 @@ int enqueue_step(lbm_ctx* ctx, int c)
         s.list = ctx->changed;
         s.cnt = ctx->cnt;
         ctx->kt->stash_fix(s, ctx->stream);
-        ++launches;
+        ctx->kt->update_masks(mask_args(ctx, true), ctx->stream);
+        launches += 2;
     }
+    if (ev) cudaEventRecord(ev[2], ctx->stream);
     return launches;
 }
 
@@ -409,6 +439,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     const int D = ctx->D;
     std::vector<PConst> pc(n);
     std::vector<PKern> pk(n);
+    std::vector<PKernF> pkf(n);
     std::vector<double> xs(3 * (size_t)n);
     for (int q = 0; q < n; ++q) {
         PConst& c = pc[q];
@@ -425,10 +456,16 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
             c.A[a] = (int)std::floor(c.x0[a]);
             k.phi[a] = c.x0[a] - (double)c.A[a];
             k.K[a] = c.A[a];
+            const int na = axis_n(ctx, a);
+            k.Kw[a] = ctx->g.wall[a] ? c.A[a] : ((c.A[a] % na) + na) % na;
             k.u[a] = (velocities && a < D) ? velocities[3 * q + a] : 0.0;
             k.om[a] = omegas ? omegas[3 * q + a] : 0.0;
             if (D == 2 && a < 2) k.om[a] = 0.0;
             xs[3 * (size_t)q + a] = c.x0[a];
+            pkf[q].u[a] = (float)k.u[a];
+            pkf[q].om[a] = (float)k.om[a];
+            pkf[q].phi[a] = (float)k.phi[a];
+            pkf[q].Kw[a] = k.Kw[a];
         }
         for (int a = 0; a < D; ++a) {
             const int na = axis_n(ctx, a);
@@ -488,11 +525,20 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     for (int q = 0; q < n; ++q) {
         pc[q].tmpl_off = (int)ctx->h_tmpl.size();
         pc[q].tmpl_n = (int)tm[q].size();
-        ctx->h_tmpl.insert(ctx->h_tmpl.end(), tm[q].begin(), tm[q].end());
+        pc[q].n_bs = pc[q].n_is = 0;
+        // grouped BS, IS, interior; lexicographic order kept inside each group
+        for (unsigned want : {CLS_BS, CLS_IS, CLS_IN})
+            for (int e : tm[q])
+                if (tmpl_cls(e) == want) {
+                    ctx->h_tmpl.push_back(e);
+                    if (want == CLS_BS) ++pc[q].n_bs;
+                    if (want == CLS_IS) ++pc[q].n_is;
+                }
         if (ctx->h_tmpl.size() >= (1ull << 31)) return fail(ctx, LBM_E_INVALID, "too many particle sites");
     }
     ctx->h_pc.insert(ctx->h_pc.end(), pc.begin(), pc.end());
     ctx->h_pk.insert(ctx->h_pk.end(), pk.begin(), pk.end());
+    ctx->h_pkf.insert(ctx->h_pkf.end(), pkf.begin(), pkf.end());
     ctx->h_x.insert(ctx->h_x.end(), xs.begin(), xs.end());
     const int first = ctx->np;
     ctx->np = tot;
@@ -505,7 +551,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
         if (it != ctx->allocs.end()) ctx->allocs.erase(it);
         cudaFree(p);
     };
-    for (void* p : {(void*)ctx->pk, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->un,
+    for (void* p : {(void*)ctx->pk, (void*)ctx->pkf, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->un,
                     (void*)ctx->acc, (void*)ctx->force, (void*)ctx->Kold, (void*)ctx->cell_of,
                     (void*)ctx->cell_count, (void*)ctx->cell_start, (void*)ctx->cell_cursor,
                     (void*)ctx->cell_items, (void*)ctx->changed, (void*)ctx->restamp,
@@ -513,6 +559,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
         release(p);
     const size_t np = (size_t)ctx->np;
     CS(dev_alloc(ctx, &ctx->pk, sizeof(PKern) * np));
+    CS(dev_alloc(ctx, &ctx->pkf, sizeof(PKernF) * np));
     CS(dev_alloc(ctx, &ctx->pc, sizeof(PConst) * np));
     CS(dev_alloc(ctx, &ctx->tmpl, sizeof(int) * ctx->h_tmpl.size()));
     CS(dev_alloc(ctx, &ctx->x, sizeof(double) * 3 * np));
@@ -531,8 +578,8 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
         CS(dev_alloc(ctx, &ctx->stash[1], (size_t)ctx->kt->compute_bytes * ctx->g.N));
         CS(dev_alloc(ctx, &ctx->cnt, sizeof(Counters)));
         CS(dev_alloc(ctx, &ctx->pairs, sizeof(unsigned long long) * PAIR_CAP));
-        if (ctx->precision == LBM_FP64)
-            CS(dev_alloc(ctx, &ctx->bs_scratch, sizeof(double) * 6 * (size_t)ctx->g.N));
+        CS(dev_alloc(ctx, &ctx->ismask, sizeof(unsigned) * (size_t)ctx->g.N));
+        CS(dev_alloc(ctx, (char**)&ctx->bs_scratch, (size_t)ctx->kt->compute_bytes * 6 * (size_t)ctx->g.N));
         CK(prepare_particle_kernels(PAIR_CAP));
     }
     // Cell grid for contact and neighbour searches: cells at least 2 r_max + gap + 4 wide.
@@ -551,6 +598,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CS(dev_alloc(ctx, &ctx->cell_cursor, sizeof(int) * (size_t)ctx->cg.total));
 
     CK(cudaMemcpyAsync(ctx->pk, ctx->h_pk.data(), sizeof(PKern) * np, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pkf, ctx->h_pkf.data(), sizeof(PKernF) * np, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->pc, ctx->h_pc.data(), sizeof(PConst) * np, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->tmpl, ctx->h_tmpl.data(), sizeof(int) * ctx->h_tmpl.size(), cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -559,6 +607,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CK(cudaMemsetAsync(ctx->force, 0, sizeof(double) * 6 * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->tag, 0xFF, sizeof(unsigned) * (size_t)ctx->g.N, ctx->stream));
     launch_stamp_all(particle_args(ctx), ctx->stream);
+    ctx->kt->update_masks(mask_args(ctx, false), ctx->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
     for (int c = 0; c < 2; ++c)
@@ -584,6 +633,38 @@ lbm_status lbm_step(lbm_ctx* ctx, int n)
         ++ctx->steps;
     }
     return LBM_OK;
+}
+
+lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3])
+{
+    if (!ctx || !out_ms || n < 1) return LBM_E_INVALID;
+    CS(ensure_alloc(ctx));
+    CS(build_graphs(ctx));
+    ctx->stepped = true;
+    std::vector<cudaEvent_t> ev(3 * (size_t)n, nullptr);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    for (int s = 0; s < n; ++s) {
+        enqueue_step(ctx, ctx->cur, &ev[3 * (size_t)s]);
+        ctx->cur ^= 1;
+        ++ctx->steps;
+    }
+    cudaError_t le = cudaGetLastError();
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    double acc[3] = {0, 0, 0};
+    for (int s = 0; s < n && le == cudaSuccess && se == cudaSuccess; ++s) {
+        float a = 0, b = 0, c = 0;
+        cudaEventElapsedTime(&a, ev[3 * (size_t)s], ev[3 * (size_t)s + 1]);
+        cudaEventElapsedTime(&b, ev[3 * (size_t)s + 1], ev[3 * (size_t)s + 2]);
+        cudaEventElapsedTime(&c, ev[3 * (size_t)s], ev[3 * (size_t)s + 2]);
+        acc[0] += a;
+        acc[1] += b;
+        acc[2] += c;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (le != cudaSuccess) return cuda_fail(ctx, le, "kernel launch");
+    if (se != cudaSuccess) return cuda_fail(ctx, se, "cudaStreamSynchronize");
+    for (int k = 0; k < 3; ++k) out_ms[k] = acc[k] / n;
+    return sync_status(ctx);
 }
 
 lbm_status lbm_synchronize(lbm_ctx* ctx)

@@ -112,8 +112,30 @@ struct __align__(16) PKern {
     double om[3];  // angular velocity omega_p
     double phi[3]; // x_p0 - floor(x_p0): lever arm of offset o is o - phi
     int K[3];      // anchor floor(x_p0) + shift: site of offset o is K + o
-    int pad;
+    int Kw[3];     // K wrapped into [0, n) on periodic axes (= K on wall axes)
 };
+
+// FP32 copy of the same record for the reduced-precision sweeps (no FP64 conversions in
+// the hot loop), refreshed by the particle phase every step.
+struct __align__(16) PKernF {
+    float u[3];
+    float om[3];
+    float phi[3];
+    int Kw[3];
+};
+
+// Lever-arm offset of site coordinate s from a wrapped anchor kw (|o| < n/2 is guaranteed
+// by the particle-size check): minimum image without a division.
+__device__ __forceinline__ int offset_from_wrapped(int s, int kw, int n, bool periodic)
+{
+    int o = s - kw;
+    if (periodic) {
+        const int h = n / 2;
+        if (o < -h) o += n;
+        else if (o >= n - h) o -= n;
+    }
+    return o;
+}
 
 // Constants of each particle.
 struct __align__(16) PConst {
@@ -121,9 +143,11 @@ struct __align__(16) PConst {
     double r, inv_m, inv_I;
     double ext[3]; // external velocity increment per step (buoyant gravity, body force)
     int A[3];      // floor(x0)
-    int tmpl_off;  // first template entry
+    int tmpl_off;  // first template entry; entries are grouped BS, IS, then interior, each
+                   // group in z, y, x lexicographic order of the offsets
     int tmpl_n;    // number of template entries
-    int pad;
+    int n_bs;      // entries [tmpl_off, tmpl_off + n_bs) are BS
+    int n_is;      // the next n_is entries are IS
 };
 
 // Device status word values (mirrors lbm_status codes).
@@ -148,8 +172,14 @@ struct Geom {
 struct PartView {
     const unsigned* tag;  // owner map [N] (nullptr when there are no particles)
     const PKern* pk;      // [np]
+    const PKernF* pkf;    // [np] FP32 copy
     const int* pending;   // 1: the IS imposition of the previous step is still to apply
+    // Per-site mask of pull directions whose source is an IS site of the site's own owner
+    // (bit i), and bit 31 when some source is an IS site of another particle.
+    const unsigned* ismask;
 };
+
+constexpr unsigned MASK_OTHER = 1u << 31;
 
 __device__ inline int wrap_offset(int o, int n, bool periodic)
 {
@@ -159,6 +189,57 @@ __device__ inline int wrap_offset(int o, int n, bool periodic)
     if (o < -h) o += n;
     else if (o >= n - h) o -= n;
     return o;
+}
+
+// Anchor wrapped into [0, n) on periodic axes (once per particle).
+__device__ __forceinline__ void wrap_anchor(const Geom& g, const int K[3], int Kw[3])
+{
+    const int n[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Kw[k] = g.wall[k] ? K[k] : ((K[k] % n[k]) + n[k]) % n[k];
+}
+
+// Site index of offset o of a particle with wrapped anchor Kw (|o| < n on periodic axes, so
+// one correction suffices); false when the site lies beyond a wall.
+__device__ __forceinline__ bool site_fast(const Geom& g, const int Kw[3], int ox, int oy, int oz,
+                                          unsigned& idx)
+{
+    int v[3] = {Kw[0] + ox, Kw[1] + oy, Kw[2] + oz};
+    const int n[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (v[k] < 0) {
+            if (g.wall[k]) return false;
+            v[k] += n[k];
+        } else if (v[k] >= n[k]) {
+            if (g.wall[k]) return false;
+            v[k] -= n[k];
+        }
+    }
+    idx = ((unsigned)v[2] * (unsigned)g.ny + (unsigned)v[1]) * (unsigned)g.nx + (unsigned)v[0];
+    return true;
+}
+
+// Same, also returning the site's coordinates.
+__device__ __forceinline__ bool site_fast_xyz(const Geom& g, const int Kw[3], int ox, int oy, int oz,
+                                              unsigned& idx, int v[3])
+{
+    v[0] = Kw[0] + ox;
+    v[1] = Kw[1] + oy;
+    v[2] = Kw[2] + oz;
+    const int n[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (v[k] < 0) {
+            if (g.wall[k]) return false;
+            v[k] += n[k];
+        } else if (v[k] >= n[k]) {
+            if (g.wall[k]) return false;
+            v[k] -= n[k];
+        }
+    }
+    idx = ((unsigned)v[2] * (unsigned)g.ny + (unsigned)v[1]) * (unsigned)g.nx + (unsigned)v[0];
+    return true;
 }
 
 // Site index of offset o of a particle anchored at K; false when it lies beyond a wall.

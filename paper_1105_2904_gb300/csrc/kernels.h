@@ -18,9 +18,9 @@ struct SweepArgs {
     PartView pv;               // tag == nullptr: no particles
     const void* stash_in;      // [N] compute type (double / float): site density (deviation)
     void* stash_out;           // [N]
-    double* acc;               // [np][6] dP, dL accumulators (FP32 storage modes)
-    double* bs_scratch;        // [N][6] per-site dP, dL (FP64 mode, fixed-order reduction)
+    void* bs_scratch;          // [N][6] per-site dP, dL at BS sites (double in FP64 mode, else float)
     double omega, pre, F[3];   // 1/tau, 1 - 1/(2 tau), body force
+    float omega_f, pre_f, F_f[3];  // the same in FP32 (reduced-storage sweeps)
 };
 
 struct MaterializeArgs {
@@ -63,8 +63,22 @@ struct StashFixArgs {
     const Counters* cnt;       // cnt->nchanged entries of list
 };
 
+struct MaskArgs {
+    int lattice;
+    Geom g;
+    const unsigned* tag;
+    unsigned* ismask;          // [N]
+    const PKern* pk;
+    const PConst* pc;
+    const int* tmpl;
+    const int* list;           // particles whose sites need new masks (nullptr = all np)
+    const Counters* cnt;       // cnt->nrestamp entries of list
+    int np;
+};
+
 struct KernelTable {
     void (*sweep)(const SweepArgs&, cudaStream_t);
+    void (*update_masks)(const MaskArgs&, cudaStream_t);
     void (*materialize)(const MaterializeArgs&, cudaStream_t);
     void (*convert_in)(const ConvertArgs&, cudaStream_t);
     void (*unstream)(const UnstreamArgs&, cudaStream_t);
@@ -91,6 +105,7 @@ struct ParticleArgs {
     Geom g;
     int np;
     PKern* pk;
+    PKernF* pkf;        // FP32 copy of pk, refreshed after the move
     const PConst* pc;
     const int* tmpl;
     unsigned* tag;
@@ -99,7 +114,8 @@ struct ParticleArgs {
     double* un;         // [np][3] velocity during the contact step
     double* acc;        // [np][6]
     double* force;      // [np][6] -dP, -dL of the last step
-    const double* bs_scratch;  // FP64 mode: per-site dP, dL (nullptr otherwise)
+    const void* bs_scratch;  // per-site dP, dL at BS sites ([N][6], double or float)
+    int scratch_f64;         // 1: bs_scratch holds doubles (FP64 mode)
     Counters* cnt;
     int* status;        // device status word (first fault wins)
     int* pending;

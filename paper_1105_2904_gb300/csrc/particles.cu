@@ -15,9 +15,13 @@ constexpr int PT = 128;  // threads per block of the per-particle kernels
 
 __device__ inline void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
+// d - n floor(d/n + 1/2). For |d| < n/4, d/n + 1/2 lies in (1/4, 3/4) whatever the
+// rounding, so the floor is 0 and the result is d itself: skip the FP64 division.
 __device__ inline double min_image(double d, int n, bool periodic)
 {
     if (!periodic) return d;
+    const double q = 0.25 * (double)n;
+    if (d > -q && d < q) return d;
     return d - (double)n * floor(d / (double)n + 0.5);
 }
 
@@ -25,27 +29,82 @@ __device__ inline int axis_len(const Geom& g, int k) { return k == 0 ? g.nx : (k
 
 __device__ inline bool periodic_axis(const Geom& g, int k, int D) { return k < D && !g.wall[k]; }
 
-// Fixed-order sum of the per-site momentum exchange of each particle: template order
-// (z, y, x lexicographic offsets), only sites the particle owns as BS (Eqs. 8-9).
+// Fixed-order sums of the per-site momentum exchange of each particle (Eqs. 8-9) over the
+// sites it owns as BS, in template order (z, y, x lexicographic offsets). FP64 mode: one
+// thread per particle, strictly sequential, the order a direct implementation uses.
 __global__ void k_reduce_ordered(const ParticleArgs a)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
     const PConst pc = a.pc[p];
-    int K[3] = {a.pk[p].K[0], a.pk[p].K[1], a.pk[p].K[2]};
+    const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
     const unsigned code = (CLS_BS << 30) | (unsigned)p;
+    const double* sc = (const double*)a.bs_scratch;
     double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int e = 0; e < pc.tmpl_n; ++e) {
+    for (int e = 0; e < pc.n_bs; ++e) {
         const int ent = a.tmpl[pc.tmpl_off + e];
-        if (tmpl_cls(ent) != CLS_BS) continue;
         unsigned site;
-        if (!site_of(a.g, K, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+        if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
         if (a.tag[site] != code) continue;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) s[q] += a.bs_scratch[(size_t)site * 6 + q];
+        for (int q = 0; q < 6; ++q) s[q] += sc[(size_t)site * 6 + q];
     }
 #pragma unroll
     for (int q = 0; q < 6; ++q) a.acc[(size_t)p * 6 + q] = s[q];
+}
+
+// FP32 modes: one block per particle. Thread t sums entries t, t + T, ... in FP32 (loads
+// of four entries in flight), then a fixed tree combines the threads (deterministic), and
+// the total is stored in FP64.
+constexpr int RT = 128;
+__global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a)
+{
+    __shared__ float part[RT / 32][6];
+    const int p = blockIdx.x;
+    const PConst pc = a.pc[p];
+    const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
+    const unsigned code = (CLS_BS << 30) | (unsigned)p;
+    const float* sc = (const float*)a.bs_scratch;
+    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int e0 = threadIdx.x; e0 < pc.n_bs; e0 += 4 * RT) {
+        unsigned site[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * RT;
+            ok[u] = false;
+            if (e < pc.n_bs) {
+                const int ent = a.tmpl[pc.tmpl_off + e];
+                ok[u] = site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site[u]);
+            }
+        }
+        unsigned t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = ok[u] ? a.tag[site[u]] : 0u;
+        float v[4][6];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v[u][q] = ok[u] ? sc[(size_t)site[u] * 6 + q] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (ok[u] && t[u] == code)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) s[q] += v[u][q];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+        if (lane == 0) part[warp][q] = s[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float tot = 0.f;
+        for (int w = 0; w < RT / 32; ++w) tot += part[w][threadIdx.x];
+        a.acc[(size_t)p * 6 + threadIdx.x] = (double)tot;
+    }
 }
 
 __device__ inline int cell_coord(const ParticleArgs& a, int k, double x)
@@ -146,9 +205,11 @@ __device__ inline int nbr_cells(const ParticleArgs& a, int k, int c, int out[3])
 }
 
 // Candidate pairs (i < j) whose predicted centres overlap: |(x_i+u_i')-(x_j+u_j')| < r_i+r_j+gap.
+// One thread per (particle, neighbouring cell): up to 27 threads per particle.
 __global__ void k_pairs(const ParticleArgs a)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / 27, cn = t % 27;
     if (i >= a.np) return;
     const int D = a.lattice == 0 ? 2 : 3;
     const int c = a.cell_of[i];
@@ -156,40 +217,39 @@ __global__ void k_pairs(const ParticleArgs a)
     int lx[3], ly[3], lz[3];
     const int nxc = nbr_cells(a, 0, cc[0], lx), nyc = nbr_cells(a, 1, cc[1], ly),
               nzc = nbr_cells(a, 2, cc[2], lz);
+    const int xx = cn % 3, yy = (cn / 3) % 3, zz = cn / 9;
+    if (xx >= nxc || yy >= nyc || zz >= nzc) return;
+    const int cell = (lz[zz] * a.cg.n[1] + ly[yy]) * a.cg.n[0] + lx[xx];
+    const int s0 = a.cell_start[cell], s1 = a.cell_start[cell + 1];
+    if (s0 == s1) return;
     const double ri = a.pc[i].r;
     double xi[3], ui[3];
     for (int k = 0; k < 3; ++k) {
         xi[k] = a.x[(size_t)i * 3 + k];
         ui[k] = a.un[(size_t)i * 3 + k];
     }
-    for (int zz = 0; zz < nzc; ++zz)
-        for (int yy = 0; yy < nyc; ++yy)
-            for (int xx = 0; xx < nxc; ++xx) {
-                const int cell = (lz[zz] * a.cg.n[1] + ly[yy]) * a.cg.n[0] + lx[xx];
-                for (int s = a.cell_start[cell]; s < a.cell_start[cell + 1]; ++s) {
-                    const int j = a.cell_items[s];
-                    if (j <= i) continue;
-                    double d2 = 0.0;
-                    for (int k = 0; k < 3; ++k) {
-                        double pd = (a.x[(size_t)j * 3 + k] + a.un[(size_t)j * 3 + k]) - (xi[k] + ui[k]);
-                        pd = min_image(pd, axis_len(a.g, k), periodic_axis(a.g, k, D));
-                        d2 += pd * pd;
-                    }
-                    const double R = ri + a.pc[j].r + a.gap;
-                    if (d2 < R * R) {
-                        const int slot = atomicAdd(&a.cnt->npairs, 1);
-                        if (slot < a.pair_cap)
-                            a.pairs[slot] = ((unsigned long long)i << 32) | (unsigned long long)j;
-                        else
-                            set_status(a.status, ERR_CAPACITY);
-                    }
-                }
-            }
+    for (int s = s0; s < s1; ++s) {
+        const int j = a.cell_items[s];
+        if (j <= i) continue;
+        double d2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double pd = (a.x[(size_t)j * 3 + k] + a.un[(size_t)j * 3 + k]) - (xi[k] + ui[k]);
+            pd = min_image(pd, axis_len(a.g, k), periodic_axis(a.g, k, D));
+            d2 += pd * pd;
+        }
+        const double R = ri + a.pc[j].r + a.gap;
+        if (d2 < R * R) {
+            const int slot = atomicAdd(&a.cnt->npairs, 1);
+            if (slot < a.pair_cap)
+                a.pairs[slot] = ((unsigned long long)i << 32) | (unsigned long long)j;
+            else
+                set_status(a.status, ERR_CAPACITY);
+        }
+    }
 }
 
-// One block: sort the candidate pairs, resolve them serially in (i, j) order, then the
-// walls, the position update, the new shifts and the list of particles whose shift changed.
-__global__ void k_resolve_move(const ParticleArgs a)
+// One block: sort the candidate pairs and resolve them serially in (i, j) order.
+__global__ void k_resolve(const ParticleArgs a)
 {
     extern __shared__ unsigned long long keys[];
     const int D = a.lattice == 0 ? 2 : 3;
@@ -242,8 +302,16 @@ __global__ void k_resolve_move(const ParticleArgs a)
             }
         }
     }
-    __syncthreads();
-    for (int p = threadIdx.x; p < a.np; p += T) {
+}
+
+// Walls, position update (Eq. 13), new shifts (Eqs. 14-15) and the list of particles whose
+// shift changed; one thread per particle.
+__global__ void k_move(const ParticleArgs a)
+{
+    const int D = a.lattice == 0 ? 2 : 3;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) *a.pending = 1;
+    if (p < a.np) {
         const PConst pc = a.pc[p];
         double* u = &a.un[(size_t)p * 3];
         double* x = &a.x[(size_t)p * 3];
@@ -272,10 +340,17 @@ __global__ void k_resolve_move(const ParticleArgs a)
             if (dK != 0) changed = true;
             if (dK > 1 || dK < -1) set_status(a.status, ERR_UNSTABLE);
             k.K[q] = Kn;
+            const int n = axis_len(a.g, q);
+            k.Kw[q] = a.g.wall[q] ? Kn : ((Kn % n) + n) % n;
+        }
+        PKernF& kf = a.pkf[p];
+        for (int q = 0; q < 3; ++q) {
+            kf.u[q] = (float)k.u[q];
+            kf.om[q] = (float)k.om[q];
+            kf.Kw[q] = k.Kw[q];
         }
         if (changed) a.changed[atomicAdd(&a.cnt->nchanged, 1)] = p;
     }
-    if (threadIdx.x == 0) *a.pending = 1;
 }
 
 __device__ inline void add_restamp(const ParticleArgs& a, int q)
@@ -331,10 +406,12 @@ __global__ void k_mark_clear(const ParticleArgs a)
         const int p = a.changed[b];
         const PConst pc = a.pc[p];
         const int K[3] = {a.Kold[(size_t)p * 3], a.Kold[(size_t)p * 3 + 1], a.Kold[(size_t)p * 3 + 2]};
+        int Kw[3];
+        wrap_anchor(a.g, K, Kw);
         for (int e = threadIdx.x; e < pc.tmpl_n; e += blockDim.x) {
             const int ent = a.tmpl[pc.tmpl_off + e];
             unsigned site;
-            if (!site_of(a.g, K, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+            if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
             const unsigned t = a.tag[site];
             if (t != TAG_FLUID && (t & PID_MASK) == (unsigned)p) a.tag[site] = TAG_FLUID;
         }
@@ -345,11 +422,11 @@ __global__ void k_mark_clear(const ParticleArgs a)
 __device__ inline void stamp_particle(const ParticleArgs& a, int p)
 {
     const PConst pc = a.pc[p];
-    const int K[3] = {a.pk[p].K[0], a.pk[p].K[1], a.pk[p].K[2]};
+    const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
     for (int e = threadIdx.x; e < pc.tmpl_n; e += blockDim.x) {
         const int ent = a.tmpl[pc.tmpl_off + e];
         unsigned site;
-        if (!site_of(a.g, K, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+        if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
         atomicMin(&a.tag[site], (tmpl_cls(ent) << 30) | (unsigned)p);
     }
 }
@@ -377,20 +454,22 @@ int launch_particle_phase(const ParticleArgs& a, cudaStream_t s)
     cudaMemsetAsync(a.cell_count, 0, sizeof(int) * (size_t)a.cg.total, s);
     cudaMemsetAsync(a.cell_cursor, 0, sizeof(int) * (size_t)a.cg.total, s);
     cudaMemsetAsync(a.restamp_flag, 0, sizeof(int) * (size_t)a.np, s);
-    if (a.bs_scratch) {
+    if (a.scratch_f64)
         k_reduce_ordered<<<blocks, PT, 0, s>>>(a);
-        ++launches;
-    }
+    else
+        k_reduce_block<<<a.np, RT, 0, s>>>(a);
+    ++launches;
     k_accel<<<blocks, PT, 0, s>>>(a);
     k_cell_scan<<<1, 1024, 0, s>>>(a);
     k_cell_fill<<<blocks, PT, 0, s>>>(a);
-    k_pairs<<<blocks, PT, 0, s>>>(a);
+    k_pairs<<<(a.np * 27 + PT - 1) / PT, PT, 0, s>>>(a);
     const size_t smem = sizeof(unsigned long long) * (size_t)a.pair_cap;
-    k_resolve_move<<<1, 1024, smem, s>>>(a);
+    k_resolve<<<1, 1024, smem, s>>>(a);
+    k_move<<<blocks, PT, 0, s>>>(a);
     k_mark_neighbours<<<blocks, PT, 0, s>>>(a);
     k_mark_clear<<<mark_grid(), 256, 0, s>>>(a);
     k_mark_stamp<<<mark_grid(), 256, 0, s>>>(a);
-    launches += 8;
+    launches += 9;
     return launches;
 }
 
@@ -401,7 +480,7 @@ void launch_stamp_all(const ParticleArgs& a, cudaStream_t s)
 
 cudaError_t prepare_particle_kernels(int pair_cap)
 {
-    return cudaFuncSetAttribute(k_resolve_move, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(unsigned long long) * (size_t)pair_cap));
 }
 

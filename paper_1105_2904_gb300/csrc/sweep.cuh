@@ -31,28 +31,51 @@ __device__ __forceinline__ void sfor(F&& f)
     }
 }
 
-// Lever arm r = (x_site - x_p) of site (sx, sy, sz) owned by particle k (Eqs. 5, 7, 12):
-// the integer offset from the anchor (minimum image on periodic axes) minus phi.
-template <typename C>
-__device__ __forceinline__ void lever_arm(const Geom& g, const PKern& k, int sx, int sy, int sz,
-                                          C r[3])
+// Lever arm r = (x_site - x_p) of site (sx, sy, sz) owned by a particle (Eqs. 5, 7, 12):
+// the integer offset from the particle's anchor (minimum image on periodic axes) minus phi.
+template <typename K, typename C>
+__device__ __forceinline__ void lever_arm(const Geom& g, const K& k, int sx, int sy, int sz, C r[3])
 {
-    const int o0 = wrap_offset(sx - k.K[0], g.nx, !g.wall[0]);
-    const int o1 = wrap_offset(sy - k.K[1], g.ny, !g.wall[1]);
-    const int o2 = wrap_offset(sz - k.K[2], g.nz, !g.wall[2]);
-    r[0] = (C)o0 - (C)k.phi[0];
-    r[1] = (C)o1 - (C)k.phi[1];
-    r[2] = (C)o2 - (C)k.phi[2];
+    const int o0 = offset_from_wrapped(sx, k.Kw[0], g.nx, !g.wall[0]);
+    const int o1 = offset_from_wrapped(sy, k.Kw[1], g.ny, !g.wall[1]);
+    const int o2 = offset_from_wrapped(sz, k.Kw[2], g.nz, !g.wall[2]);
+    r[0] = (C)o0 - k.phi[0];
+    r[1] = (C)o1 - k.phi[1];
+    r[2] = (C)o2 - k.phi[2];
 }
 
 // Rigid-body velocity u_p + omega_p x r (Eq. 5 / Eq. 12, read as a rigid-body motion).
-template <typename C>
-__device__ __forceinline__ void rigid_velocity(const PKern& k, const C r[3], C out[3])
+template <typename K, typename C>
+__device__ __forceinline__ void rigid_velocity(const K& k, const C r[3], C out[3])
 {
-    const C om0 = (C)k.om[0], om1 = (C)k.om[1], om2 = (C)k.om[2];
-    out[0] = (C)k.u[0] + (om1 * r[2] - om2 * r[1]);
-    out[1] = (C)k.u[1] + (om2 * r[0] - om0 * r[2]);
-    out[2] = (C)k.u[2] + (om0 * r[1] - om1 * r[0]);
+    out[0] = k.u[0] + (k.om[1] * r[2] - k.om[2] * r[1]);
+    out[1] = k.u[1] + (k.om[2] * r[0] - k.om[0] * r[2]);
+    out[2] = k.u[2] + (k.om[0] * r[1] - k.om[1] * r[0]);
+}
+
+// Compile-time masks of the directions whose component k equals v.
+template <class L>
+__host__ __device__ constexpr unsigned dir_mask(int k, int v)
+{
+    unsigned m = 0;
+    for (int i = 0; i < L::Q; ++i)
+        if (L::c(i, k) == v) m |= 1u << i;
+    return m;
+}
+template <class L>
+__device__ __forceinline__ int c_rt(int i, int k)
+{
+    return (int)((dir_mask<L>(k, 1) >> i) & 1u) - (int)((dir_mask<L>(k, -1) >> i) & 1u);
+}
+template <class L>
+__device__ __forceinline__ float w_rt(int i)
+{
+    constexpr unsigned axis = dir_mask<L>(0, 0) & dir_mask<L>(1, 0) & dir_mask<L>(2, 0);  // rest only
+    unsigned lvl1 = 0;
+    for (int j = 1; j < L::Q; ++j)
+        if (L::c(j, 0) * L::c(j, 0) + L::c(j, 1) * L::c(j, 1) + L::c(j, 2) * L::c(j, 2) == 1) lvl1 |= 1u << j;
+    if ((axis >> i) & 1u) return (float)L::w(0);
+    return ((lvl1 >> i) & 1u) ? (float)L::w(1) : (float)L::w(L::Q - 1);
 }
 
 // Equilibrium of direction i, or of opp(i) when sgn < 0 (c_opp = -c_i), at density rho
@@ -106,12 +129,21 @@ __device__ __forceinline__ void collide_plain(double f[], const SweepArgs& a)
     });
 }
 
-// BGK collision with Guo forcing on deviations g = f - w (FP32).
+// BGK collision with Guo forcing on deviations g = f - w (FP32). Opposite directions i and
+// opp(i) share the even part of the equilibrium and of the forcing term and differ by the
+// sign of the odd part, so each pair is relaxed together:
+//   g*_i = (1 - omega) g_i + A + B,  g*_opp(i) = (1 - omega) g_opp(i) + A - B,
+//   A = omega w (drho + rho (4.5 (c.u)^2 - 1.5 u^2)) + pre w (9 (c.u)(c.F) - 3 u.F),
+//   B = 3 omega w rho (c.u) + 3 pre w (c.F).
 template <class L>
-__device__ __forceinline__ void collide_dev(float g[], const SweepArgs& a)
+__device__ __forceinline__ void collide_dev(float g[], const SweepArgs& a, float& drho, float& j0, float& j1,
+                                            float& j2)
 {
     constexpr int Q = L::Q;
-    float drho = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
+    drho = 0.0f;
+    j0 = 0.0f;
+    j1 = 0.0f;
+    j2 = 0.0f;
     sfor<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         drho += g[i];
@@ -119,21 +151,52 @@ __device__ __forceinline__ void collide_dev(float g[], const SweepArgs& a)
         if constexpr (L::c(i, 1) != 0) j1 += (float)L::c(i, 1) * g[i];
         if constexpr (L::c(i, 2) != 0) j2 += (float)L::c(i, 2) * g[i];
     });
-    const float F0 = (float)a.F[0], F1 = (float)a.F[1], F2 = (float)a.F[2];
+    const float F0 = a.F_f[0], F1 = a.F_f[1], F2 = a.F_f[2];
     const float rho = 1.0f + drho;
     const float inv = 1.0f / rho;
     const float u[3] = {(j0 + 0.5f * F0) * inv, (j1 + 0.5f * F1) * inv, (j2 + 0.5f * F2) * inv};
-    const float omega = (float)a.omega, pre = (float)a.pre;
-    const float uF = u[0] * F0 + u[1] * F1 + u[2] * F2;
+    const float omega = a.omega_f, pre = a.pre_f, om1 = 1.0f - omega;
+    const float uF3 = 3.0f * (u[0] * F0 + u[1] * F1 + u[2] * F2);
     const float usq15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    sfor<0, Q>([&](auto ic) {
+    {   // rest direction
+        const float w = (float)L::w(0);
+        g[0] = om1 * g[0] + omega * w * (drho - rho * usq15) - pre * w * uF3;
+    }
+    sfor<1, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        const float cu = (float)L::c(i, 0) * u[0] + (float)L::c(i, 1) * u[1] + (float)L::c(i, 2) * u[2];
-        const float cF = (float)L::c(i, 0) * F0 + (float)L::c(i, 1) * F1 + (float)L::c(i, 2) * F2;
-        const float w = (float)L::w(i);
-        const float geq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
-        const float Si = pre * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
-        g[i] = g[i] - omega * (g[i] - geq) + Si;
+        constexpr int j = L::opp(i);
+        if constexpr (j > i) {
+            const float cu = (float)L::c(i, 0) * u[0] + (float)L::c(i, 1) * u[1] + (float)L::c(i, 2) * u[2];
+            const float cF = (float)L::c(i, 0) * F0 + (float)L::c(i, 1) * F1 + (float)L::c(i, 2) * F2;
+            const float w = (float)L::w(i);
+            const float ow = omega * w, pw = pre * w;
+            const float A = ow * (drho + rho * (4.5f * cu * cu - usq15)) + pw * (9.0f * cu * cF - uF3);
+            const float B = 3.0f * (ow * rho * cu + pw * cF);
+            g[i] = om1 * g[i] + (A + B);
+            g[j] = om1 * g[j] + (A - B);
+        }
+    });
+}
+
+// All equilibrium deviations g^eq_i(drho, u) (FP32), by opposite pairs.
+template <class L>
+__device__ __forceinline__ void equilibrium_dev(float drho, const float u[3], float g[])
+{
+    constexpr int Q = L::Q;
+    const float rho = 1.0f + drho;
+    const float usq15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    g[0] = (float)L::w(0) * (drho - rho * usq15);
+    sfor<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int j = L::opp(i);
+        if constexpr (j > i) {
+            const float cu = (float)L::c(i, 0) * u[0] + (float)L::c(i, 1) * u[1] + (float)L::c(i, 2) * u[2];
+            const float w = (float)L::w(i);
+            const float even = w * (drho + rho * (4.5f * cu * cu - usq15));
+            const float odd = 3.0f * w * rho * cu;
+            g[i] = even + odd;
+            g[j] = even - odd;
+        }
     });
 }
 
@@ -200,16 +263,22 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, const Geom& g, c
     });
 }
 
-// Applies the pending IS imposition to the pulled values of a site inside a particle.
-template <class L, typename S, bool WALLS>
-__device__ __forceinline__ void substitute_is(const Geom& g, const Nbr& n, int x, int y, int z,
-                                              unsigned idx, const PartView& pv,
-                                              const typename Store<S>::C* __restrict__ stash,
-                                              typename Store<S>::C f[])
+// Applies the pending IS imposition (Eq. 12) to the values a site inside a particle pulls:
+// a value pulled from an IS site s in direction i becomes f^eq(rho_I(s), u_p + omega_p x r(s))
+// of the stored direction. `m` is the site's IS-source mask (bit i: the source of direction
+// i is an IS site of the site's own owner; MASK_OTHER: some source belongs to another
+// particle).
+//
+// FP64 form: every substituted value is recomputed from its own lever arm, exactly as a
+// direct implementation of Eq. 12 does.
+template <class L, bool WALLS>
+__device__ __forceinline__ void substitute_is_plain(const Geom& g, const Nbr& n, int x, int y, int z,
+                                                    unsigned idx, unsigned m, const PartView& pv,
+                                                    const double* __restrict__ stash, double f[])
 {
-    using C = typename Store<S>::C;
     sfor<0, L::Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
+        if ((m & (MASK_OTHER | (1u << i))) == 0) return;
         int sx, sy, sz;
         unsigned sidx;
         bool bounce;
@@ -217,16 +286,123 @@ __device__ __forceinline__ void substitute_is(const Geom& g, const Nbr& n, int x
         const unsigned t = pv.tag[sidx];
         if ((t >> 30) == CLS_IS) {
             const PKern& k = pv.pk[t & PID_MASK];
-            C r[3], uI[3];
-            lever_arm<C>(g, k, sx, sy, sz, r);
-            rigid_velocity<C>(k, r, uI);
-            const C sgn = bounce ? (C)-1 : (C)1;
-            if constexpr (Store<S>::deviation)
-                f[i] = geq_dev<L, i>(sgn, stash[sidx], uI);
-            else
-                f[i] = feq_plain<L, i>(sgn, stash[sidx], uI);
+            double r[3], uI[3];
+            lever_arm(g, k, sx, sy, sz, r);
+            rigid_velocity(k, r, uI);
+            f[i] = feq_plain<L, i>(bounce ? -1.0 : 1.0, stash[sidx], uI);
         }
     });
+}
+
+// FP32 form. With u(s) = u(x) - omega x c_i for the source s = x - c_i of a rigid motion:
+// c_i.u(s) = c_i.u(x) (c_i.(omega x c_i) = 0) and
+// |u(s)|^2 = |u(x)|^2 - 2 c_i.(u(x) x omega) + |omega|^2 |c_i|^2 - (omega.c_i)^2,
+// so one rigid velocity per site serves all of its sources.
+template <class L, bool WALLS>
+__device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, int x, int y, int z,
+                                                  unsigned idx, unsigned m, unsigned owner,
+                                                  const PartView& pv, const float* __restrict__ stash,
+                                                  float f[])
+{
+    constexpr int Q = L::Q;
+    if (m & ~MASK_OTHER) {
+        const PKernF k = pv.pkf[owner];
+        float r[3], ux[3];
+        lever_arm(g, k, x, y, z, r);
+        rigid_velocity(k, r, ux);
+        const float a0 = ux[1] * k.om[2] - ux[2] * k.om[1];   // u(x) x omega
+        const float a1 = ux[2] * k.om[0] - ux[0] * k.om[2];
+        const float a2 = ux[0] * k.om[1] - ux[1] * k.om[0];
+        const float usq = ux[0] * ux[0] + ux[1] * ux[1] + ux[2] * ux[2];
+        const float w2 = k.om[0] * k.om[0] + k.om[1] * k.om[1] + k.om[2] * k.om[2];
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            if (m & (1u << i)) {
+                int sx, sy, sz;
+                unsigned sidx;
+                bool bounce;
+                pull_source<L, i, WALLS>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
+                constexpr float cx = (float)L::c(i, 0), cy = (float)L::c(i, 1), cz = (float)L::c(i, 2);
+                constexpr float c2 = cx * cx + cy * cy + cz * cz;
+                float cu = cx * ux[0] + cy * ux[1] + cz * ux[2];
+                float us = usq;
+                if (bounce) {
+                    cu = -cu;   // the source is x itself, stored direction opp(i)
+                } else {
+                    const float ca = cx * a0 + cy * a1 + cz * a2;
+                    const float cw = cx * k.om[0] + cy * k.om[1] + cz * k.om[2];
+                    us = usq - 2.0f * ca + w2 * c2 - cw * cw;
+                }
+                const float drho = stash[sidx];
+                f[i] = (float)L::w(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * us));
+            }
+        });
+    }
+    if (m & MASK_OTHER) {
+        // Sources owned by another particle (site sets of close particles meet): rare.
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) {
+            const int cx = c_rt<L>(i, 0), cy = c_rt<L>(i, 1), cz = c_rt<L>(i, 2);
+            int sx = cx > 0 ? n.xm : (cx < 0 ? n.xp : x);
+            int sy = cy > 0 ? n.ym : (cy < 0 ? n.yp : y);
+            int sz = cz > 0 ? n.zm : (cz < 0 ? n.zp : z);
+            bool bounce = false;
+            if (WALLS)
+                bounce = (cx > 0 && n.bxm) || (cx < 0 && n.bxp) || (cy > 0 && n.bym) || (cy < 0 && n.byp) ||
+                         (cz > 0 && n.bzm) || (cz < 0 && n.bzp);
+            if (bounce) { sx = x; sy = y; sz = z; }
+            const unsigned sidx = ((unsigned)sz * (unsigned)g.ny + (unsigned)sy) * (unsigned)g.nx + (unsigned)sx;
+            const unsigned t = pv.tag[sidx];
+            if ((t >> 30) != CLS_IS || (t & PID_MASK) == owner) continue;
+            const PKernF k = pv.pkf[t & PID_MASK];
+            float r[3], us[3];
+            lever_arm(g, k, sx, sy, sz, r);
+            rigid_velocity(k, r, us);
+            const float sgn = bounce ? -1.0f : 1.0f;
+            const float cu = sgn * ((float)cx * us[0] + (float)cy * us[1] + (float)cz * us[2]);
+            const float usq = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
+            const float drho = stash[sidx];
+            const float val = w_rt<L>(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+            sfor<0, Q>([&](auto jc) {
+                if (i == decltype(jc)::value) f[decltype(jc)::value] = val;
+            });
+        }
+    }
+}
+
+// Rebuilds the IS-source masks at the sites of the listed particles (their site sets hold
+// every site whose mask can be non-zero or can have changed).
+template <class L>
+__global__ void k_update_masks(const MaskArgs a)
+{
+    const int count = a.list ? a.cnt->nrestamp : a.np;
+    const Geom& g = a.g;
+    for (int b = blockIdx.x; b < count; b += gridDim.x) {
+        const int p = a.list ? a.list[b] : b;
+        const PConst pc = a.pc[p];
+        const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
+        for (int e = threadIdx.x; e < pc.tmpl_n; e += blockDim.x) {
+            const int ent = a.tmpl[pc.tmpl_off + e];
+            unsigned idx;
+            int v[3];
+            if (!site_fast_xyz(g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), idx, v)) continue;
+            const unsigned t0 = a.tag[idx];
+            const unsigned owner = t0 & PID_MASK;
+            const int x = v[0], y = v[1], z = v[2];
+            const Nbr n = neighbours<true>(g, x, y, z);
+            unsigned m = 0;
+            sfor<0, L::Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                int sx, sy, sz;
+                unsigned sidx;
+                bool bounce;
+                pull_source<L, i, true>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
+                const unsigned t = a.tag[sidx];
+                if ((t >> 30) == CLS_IS) m |= ((t & PID_MASK) == owner) ? (1u << i) : MASK_OTHER;
+            });
+            a.ismask[idx] = m;
+        }
+    }
 }
 
 template <class L, typename S, bool WALLS, bool PART>
@@ -236,26 +412,71 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
     using C = typename St::C;
     constexpr int Q = L::Q;
     const Geom& g = a.g;
-    const int xr = blockIdx.x * SWEEP_THREADS + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned row = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx;
+    int lane_site = threadIdx.x;  // which of the block's 128 sites this thread updates
+    unsigned tagx = TAG_FLUID;
+    if constexpr (PART) {
+        // Block-level counting sort of the block's sites by kind (BS, IS, other solid,
+        // fluid, beyond the row): solid-site work is then packed into as few warps as
+        // possible instead of diverging inside every warp that crosses a particle. All
+        // sites of the block stay in the same 128-site window, so memory traffic is
+        // unchanged.
+        __shared__ unsigned s_tag[SWEEP_THREADS];
+        __shared__ unsigned char s_site[SWEEP_THREADS];
+        __shared__ int s_cnt[SWEEP_THREADS / 32][5];
+        const int xr0 = blockIdx.x * SWEEP_THREADS + threadIdx.x;
+        const unsigned t0 = xr0 < g.nx ? a.pv.tag[row + (unsigned)xr0] : TAG_FLUID;
+        const unsigned c0 = t0 >> 30;
+        const int key = xr0 >= g.nx ? 4 : (c0 == CLS_BS ? 0 : (c0 == CLS_IS ? 1 : (c0 == CLS_IN ? 2 : 3)));
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const unsigned lt = (1u << lane) - 1u;
+        int rank = 0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            const unsigned b = __ballot_sync(0xffffffffu, key == v);
+            if (key == v) rank = __popc(b & lt);
+            if (lane == 0) s_cnt[warp][v] = __popc(b);
+        }
+        __syncthreads();
+        int off = 0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+#pragma unroll
+            for (int w = 0; w < SWEEP_THREADS / 32; ++w)
+                if (v < key || (v == key && w < warp)) off += s_cnt[w][v];
+        s_site[off + rank] = (unsigned char)threadIdx.x;
+        s_tag[off + rank] = t0;
+        __syncthreads();
+        lane_site = s_site[threadIdx.x];
+        tagx = s_tag[threadIdx.x];
+    }
+    const int xr = blockIdx.x * SWEEP_THREADS + lane_site;
     const bool valid = xr < g.nx;
     const int x = valid ? xr : g.nx - 1;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const unsigned idx = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
+    const unsigned idx = row + (unsigned)x;
     const size_t N = g.N;
     const Nbr n = neighbours<WALLS>(g, x, y, z);
 
     C f[Q];
     pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
 
-    unsigned tagx = TAG_FLUID;
     if constexpr (PART) {
-        tagx = a.pv.tag[idx];
-        if (tagx != TAG_FLUID && *a.pv.pending)
-            substitute_is<L, S, WALLS>(g, n, x, y, z, idx, a.pv, (const C*)a.stash_in, f);
+        if (tagx != TAG_FLUID && *a.pv.pending) {
+            const unsigned m = a.pv.ismask[idx];
+            if (m) {
+                if constexpr (St::deviation)
+                    substitute_is_dev<L, WALLS>(g, n, x, y, z, idx, m, tagx & PID_MASK, a.pv,
+                                                (const float*)a.stash_in, f);
+                else
+                    substitute_is_plain<L, WALLS>(g, n, x, y, z, idx, m, a.pv, (const double*)a.stash_in, f);
+            }
+        }
     }
 
+    float mrho = 0.f, mj0 = 0.f, mj1 = 0.f, mj2 = 0.f;  // pre-collision moments (FP32 path)
     if constexpr (St::deviation)
-        collide_dev<L>(f, a);
+        collide_dev<L>(f, a, mrho, mj0, mj1, mj2);
     else
         collide_plain<L>(f, a);
 
@@ -265,31 +486,31 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
         C dv[6] = {0, 0, 0, 0, 0, 0};
         const bool isbs = valid && cls == CLS_BS;
         if (isbs) {
-            const PKern& k = a.pv.pk[tagx & PID_MASK];
             C r[3], ub[3], ubp[3], du[3];
-            lever_arm<C>(g, k, x, y, z, r);
-            rigid_velocity<C>(k, r, ubp);
             if constexpr (St::deviation) {
-                float drho = 0.0f, j0 = 0.0f, j1 = 0.0f, j2 = 0.0f;
-                sfor<0, Q>([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    drho += f[i];
-                    if constexpr (L::c(i, 0) != 0) j0 += (float)L::c(i, 0) * f[i];
-                    if constexpr (L::c(i, 1) != 0) j1 += (float)L::c(i, 1) * f[i];
-                    if constexpr (L::c(i, 2) != 0) j2 += (float)L::c(i, 2) * f[i];
-                });
+                const PKernF k = a.pv.pkf[tagx & PID_MASK];
+                lever_arm(g, k, x, y, z, r);
+                rigid_velocity(k, r, ubp);
+            } else {
+                const PKern& k = a.pv.pk[tagx & PID_MASK];
+                lever_arm(g, k, x, y, z, r);
+                rigid_velocity(k, r, ubp);
+            }
+            if constexpr (St::deviation) {
+                // The forced collision keeps the density and adds F to the momentum, so the
+                // post-collision rho_B and rho_B u_B are rho and j + F of the pulled values.
+                const float drho = mrho;
                 const float rho = 1.0f + drho;
-                ub[0] = j0 / rho; ub[1] = j1 / rho; ub[2] = j2 / rho;
-                sfor<0, Q>([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    f[i] = geq_dev<L, i>(1.0f, drho, ubp);
-                });
+                const float pB[3] = {mj0 + a.F_f[0], mj1 + a.F_f[1], mj2 + a.F_f[2]};
+                equilibrium_dev<L>(drho, ubp, f);
+                // dp = rho_B (u_B' - u_B) = rho u_B' - (j + F); dl = r x dp (Eqs. 6-7)
 #pragma unroll
-                for (int q = 0; q < 3; ++q) du[q] = ubp[q] - ub[q];
-                dv[0] = rho * du[0]; dv[1] = rho * du[1]; dv[2] = rho * du[2];
-                dv[3] = rho * (r[1] * du[2] - r[2] * du[1]);
-                dv[4] = rho * (r[2] * du[0] - r[0] * du[2]);
-                dv[5] = rho * (r[0] * du[1] - r[1] * du[0]);
+                for (int q = 0; q < 3; ++q) dv[q] = rho * ubp[q] - pB[q];
+                dv[3] = r[1] * dv[2] - r[2] * dv[1];
+                dv[4] = r[2] * dv[0] - r[0] * dv[2];
+                dv[5] = r[0] * dv[1] - r[1] * dv[0];
+                (void)ub;
+                (void)du;
             } else {
                 double rhoB = 0.0;
                 sfor<0, Q>([&](auto ic) { rhoB += f[decltype(ic)::value]; });
@@ -319,50 +540,28 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
                 }
             }
         }
-        // Per-particle sums (Eqs. 8-9).
-        if constexpr (St::deviation) {
-            // Warp-aggregated: one FP64 atomic per (warp, particle, component).
-            const unsigned lane = threadIdx.x & 31u;
-            const unsigned pid = tagx & PID_MASK;
-            unsigned m = __ballot_sync(0xffffffffu, isbs);
-            while (m) {
-                const int leader = __ffs(m) - 1;
-                const unsigned lp = __shfl_sync(0xffffffffu, pid, leader);
-                const bool mine = isbs && pid == lp;
-                float v[6];
+        // Per-site contributions; the per-particle sums (Eqs. 8-9) are taken afterwards in
+        // a fixed order by the particle phase.
+        if (isbs) {
+            C* sc = (C*)a.bs_scratch + (size_t)idx * 6;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    v[q] = mine ? (float)dv[q] : 0.0f;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
-                }
-                if ((int)lane == leader) {
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) atomicAdd(&a.acc[(size_t)lp * 6 + q], (double)v[q]);
-                }
-                m &= ~__ballot_sync(0xffffffffu, mine);
-            }
-        } else {
-            if (isbs) {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) a.bs_scratch[(size_t)idx * 6 + q] = (double)dv[q];
-            }
+            for (int q = 0; q < 6; ++q) sc[q] = dv[q];
         }
     }
 
     if (!valid) return;
     S* __restrict__ fout = (S*)a.fout;
+    // Post-collision density of IS sites, for the IS imposition pulled next step: the sum
+    // of the values as stored.
+    const bool isis = PART && (tagx >> 30) == CLS_IS;
     C dens = (C)0;
     sfor<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         const S s = St::save(f[i], (C)L::w(i));
         fout[(size_t)i * N + idx] = s;
-        if constexpr (PART) dens += St::load(s, (C)L::w(i));
+        if (isis) dens += St::load(s, (C)L::w(i));
     });
-    if constexpr (PART) {
-        // Post-collision density of IS sites, for the IS imposition pulled next step.
-        if ((tagx >> 30) == CLS_IS) ((C*)a.stash_out)[idx] = dens;
-    }
+    if (isis) ((C*)a.stash_out)[idx] = dens;
 }
 
 template <class L, typename S, bool WALLS>
@@ -381,8 +580,16 @@ __global__ void k_materialize(const MaterializeArgs a)
     const Nbr n = neighbours<WALLS>(g, x, y, z);
     C f[Q];
     pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
-    if (a.pv.tag != nullptr && a.pv.tag[idx] != TAG_FLUID && *a.pv.pending)
-        substitute_is<L, S, WALLS>(g, n, x, y, z, idx, a.pv, (const C*)a.stash_in, f);
+    if (a.pv.tag != nullptr && a.pv.tag[idx] != TAG_FLUID && *a.pv.pending) {
+        const unsigned m = a.pv.ismask[idx];
+        if (m) {
+            if constexpr (St::deviation)
+                substitute_is_dev<L, WALLS>(g, n, x, y, z, idx, m, a.pv.tag[idx] & PID_MASK, a.pv,
+                                            (const float*)a.stash_in, f);
+            else
+                substitute_is_plain<L, WALLS>(g, n, x, y, z, idx, m, a.pv, (const double*)a.stash_in, f);
+        }
+    }
     double fd[Q];
     sfor<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
@@ -498,12 +705,11 @@ __global__ void k_stash_fix(const StashFixArgs a)
     for (int b = blockIdx.x; b < nlist; b += gridDim.x) {
         const int p = a.list[b];
         const PConst pc = a.pc[p];
-        const PKern& k = a.pk[p];
-        for (int e = threadIdx.x; e < pc.tmpl_n; e += blockDim.x) {
+        const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
+        for (int e = pc.n_bs + threadIdx.x; e < pc.n_bs + pc.n_is; e += blockDim.x) {
             const int ent = a.tmpl[pc.tmpl_off + e];
-            if (tmpl_cls(ent) != CLS_IS) continue;
             unsigned site;
-            if (!site_of(a.g, k.K, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+            if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
             C s = (C)0;
             sfor<0, L::Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
@@ -580,9 +786,16 @@ void launch_stash_fix(const StashFixArgs& a, cudaStream_t s)
 }
 
 template <typename S>
+void launch_update_masks(const MaskArgs& a, cudaStream_t s)
+{
+    if (a.lattice == 0) k_update_masks<D2Q9><<<304, 128, 0, s>>>(a);
+    else k_update_masks<D3Q19><<<304, 128, 0, s>>>(a);
+}
+
+template <typename S>
 const KernelTable* make_table()
 {
-    static const KernelTable t = {launch_sweep<S>,     launch_materialize<S>, launch_convert_in<S>,
+    static const KernelTable t = {launch_sweep<S>,     launch_update_masks<S>, launch_materialize<S>, launch_convert_in<S>,
                                   launch_unstream<S>,  launch_fill_rest<S>,   launch_stash_fix<S>,
                                   (int)sizeof(S),      (int)sizeof(typename Store<S>::C)};
     return &t;

@@ -25,7 +25,7 @@ LBM_PERIODIC, LBM_NOSLIP = 0, 1
 
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
-            "lbm_get_masks", "lbm_get_info", "lbm_last_error", "lbm_destroy")
+            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_last_error", "lbm_destroy")
 
 
 class LbmError(RuntimeError):
@@ -60,6 +60,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_set_distributions.argtypes = [P, D]
     lib.lbm_get_masks.argtypes = [P, ctypes.POINTER(ctypes.c_uint)]
     lib.lbm_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbm_profile_steps.argtypes = [P, i32, D]
     lib.lbm_last_error.argtypes = [P]
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_destroy.argtypes = [P]
@@ -170,6 +171,12 @@ def lbm_get_info(h):
     return dict(zip(keys, list(out)))
 
 
+def lbm_profile_steps(h, n):
+    out = np.zeros(3)
+    _check(h, load().lbm_profile_steps(h, int(n), _dp(out)))
+    return {"sweep_ms": float(out[0]), "particle_ms": float(out[1]), "step_ms": float(out[2])}
+
+
 def lbm_last_error(h):
     m = load().lbm_last_error(h)
     return m.decode(errors="replace") if m else ""
@@ -238,3 +245,6 @@ class Simulation:
 
     def info(self):
         return lbm_get_info(self.h)
+
+    def profile(self, n):
+        return lbm_profile_steps(self.h, n)
