@@ -152,6 +152,50 @@ lbm_status lbm_get_info(lbm_ctx* ctx, long long out[6]);
  * synchronizes. Errors as lbm_step; LBM_E_INVALID if n < 1 or out_ms is NULL. */
 lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3]);
 
+/* Largest particle count lbm_bs_exchange_noalloc accepts. */
+#define LBM_NOALLOC_MAX_PARTICLES 65536
+
+/* Boundary-site momentum exchange without any device allocation.
+ *
+ * The paper has no counterpart of this call; it exists for callers that cannot call
+ * cudaMalloc: code that owns its device memory through its own pool or arena (a host
+ * framework that forbids foreign allocations), code running where allocation is not
+ * allowed or must not stall (a real-time loop, work being recorded into a CUDA graph),
+ * and callers holding the state in buffers they allocated themselves. They pass every
+ * input and output; the library uses no memory of its own beyond a fixed array that is
+ * part of the library's device image.
+ *
+ * Computes, for a state given by the caller, what one step hands each particle through its
+ * boundary sites: at every site the owner map tags BS of particle p, the post-collision
+ * density and momentum (rho and sum_i f_i c_i + F) meet the rigid-body velocity
+ * u_p + omega_p x r, r the minimum-image offset of the site from centers[p]; the momentum
+ * change of the fluid there is summed per particle and returned as force = -sum dp and
+ * torque = -sum r x dp (the force and torque lbm_get_particles reports for a step taken
+ * from that state).
+ *
+ * Arguments: lattice and sizes as lbm_create; walls[3] (may be NULL: all periodic) flags the
+ * axes with solid walls (no minimum image there); body_force[3] the fluid force density F
+ * (may be NULL). Device pointers, caller-owned: g[Q][N] FP32 deviations f_i - w_i of the
+ * populations at the start of the step (velocity order and site order as in this header),
+ * tags[N] the owner map in the encoding of lbm_get_masks, centers / velocities / omegas
+ * [n][3] doubles, force / torque [n][3] doubles written by the call. cuda_stream: the
+ * stream the work is enqueued on (NULL = default stream); the call returns after enqueueing.
+ *
+ * Limits and rules: n <= LBM_NOALLOC_MAX_PARTICLES, else LBM_E_INVALID (as for sizes
+ * lbm_create rejects). The per-particle accumulators live in one fixed device array (3 MiB,
+ * held by every GPU that loads the library until the process exits) shared by all calls:
+ * each call clears the part it uses before accumulating, and the array keeps the last
+ * call's sums afterwards. Calls that overlap on the GPU (different streams, or devices
+ * sharing nothing else) race on that array and must be serialised by the caller. The first
+ * call on each device looks up the array's device address (a CUDA runtime query, no
+ * allocation); make that first call before any stream capture. No cudaMalloc, cudaFree or
+ * allocating library routine is called. LBM_E_CUDA if the device query or a launch fails. */
+lbm_status lbm_bs_exchange_noalloc(int lattice, int nx, int ny, int nz, const int walls[3],
+                                   const double body_force[3], const float* g,
+                                   const unsigned* tags, int n, const double* centers,
+                                   const double* velocities, const double* omegas,
+                                   double* force, double* torque, void* cuda_stream);
+
 /* Description of the last non-OK status of ctx (static storage; never NULL). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

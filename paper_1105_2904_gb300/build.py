@@ -1,9 +1,10 @@
 """Builds the CUDA library ``liblbmp.so`` in-tree for sm_103a (GB300).
 
-Four translation units are compiled in parallel with nvcc, one ``-gencode`` each:
+Five translation units are compiled in parallel with nvcc, one ``-gencode`` each:
 ``api.cu`` (host C-ABI; host code with -ffp-contract=off), ``sweep_f64.cu`` and
 ``particles.cu`` (-fmad=false: FP64 arithmetic evaluated exactly as written),
-``sweep_lp.cu`` (FP32 / FP16 / BF16 storage). Output: ``paper_1105_2904_gb300/_lib/``.
+``sweep_lp.cu`` (FP32 / FP16 / BF16 storage), ``noalloc.cu`` (the allocation-free boundary-site
+exchange). Output: ``paper_1105_2904_gb300/_lib/``.
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ UNITS = {
     "sweep_f64.cu": ["-fmad=false"],
     "particles.cu": ["-fmad=false"],
     "sweep_lp.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -25,7 +25,8 @@ LBM_PERIODIC, LBM_NOSLIP = 0, 1
 
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
-            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_last_error", "lbm_destroy")
+            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_bs_exchange_noalloc",
+            "lbm_last_error", "lbm_destroy")
 
 
 class LbmError(RuntimeError):
@@ -61,6 +62,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_get_masks.argtypes = [P, ctypes.POINTER(ctypes.c_uint)]
     lib.lbm_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.lbm_profile_steps.argtypes = [P, i32, D]
+    lib.lbm_bs_exchange_noalloc.argtypes = [i32, i32, i32, i32, I, D, P, P, i32, P, P, P, P, P, P]
     lib.lbm_last_error.argtypes = [P]
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_destroy.argtypes = [P]
@@ -175,6 +177,22 @@ def lbm_profile_steps(h, n):
     out = np.zeros(3)
     _check(h, load().lbm_profile_steps(h, int(n), _dp(out)))
     return {"sweep_ms": float(out[0]), "particle_ms": float(out[1]), "step_ms": float(out[2])}
+
+
+def lbm_bs_exchange_noalloc(lattice, nx, ny, nz, walls, body_force, g_ptr, tags_ptr, n, centers_ptr,
+                            velocities_ptr, omegas_ptr, force_ptr, torque_ptr, cuda_stream=None):
+    """Allocation-free boundary-site momentum exchange on caller-owned device buffers
+    (integer device addresses, e.g. torch ``data_ptr()``); see include/lbmp.h."""
+    wa = None if walls is None else np.ascontiguousarray(walls, dtype=np.int32).reshape(3)
+    F = _f64(body_force, 3)
+    st = load().lbm_bs_exchange_noalloc(
+        int(lattice), int(nx), int(ny), int(nz),
+        None if wa is None else wa.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(F),
+        ctypes.c_void_p(g_ptr), ctypes.c_void_p(tags_ptr), int(n), ctypes.c_void_p(centers_ptr),
+        ctypes.c_void_p(velocities_ptr), ctypes.c_void_p(omegas_ptr), ctypes.c_void_p(force_ptr),
+        ctypes.c_void_p(torque_ptr), ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_bs_exchange_noalloc(n=%d)" % n)
 
 
 def lbm_last_error(h):
