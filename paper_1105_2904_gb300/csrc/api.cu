@@ -57,6 +57,7 @@ struct lbm_ctx {
     Counters* cnt = nullptr;
     int* status = nullptr;
     int* pending = nullptr;
+    unsigned* step_id = nullptr;
     CellGrid cg{};
     int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_cursor = nullptr,
         *cell_items = nullptr;
@@ -136,9 +137,11 @@ lbm_status ensure_alloc(lbm_ctx* ctx)
     CS(dev_alloc(ctx, &ctx->f[1], fbytes));
     CS(dev_alloc(ctx, &ctx->status, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->pending, sizeof(int)));
+    CS(dev_alloc(ctx, &ctx->step_id, sizeof(unsigned)));
     CS(dev_alloc(ctx, &ctx->staging, STAGING_BYTES));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(ctx->pending, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(ctx->step_id, 0, sizeof(unsigned), ctx->stream));
     ctx->kt->fill_rest(ctx->lattice, ctx->f[0], ctx->g.N, ctx->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
@@ -232,6 +235,7 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     a.cnt = ctx->cnt;
     a.status = ctx->status;
     a.pending = ctx->pending;
+    a.step_id = ctx->step_id;
     a.cg = ctx->cg;
     a.cell_of = ctx->cell_of;
     a.cell_count = ctx->cell_count;
@@ -271,6 +275,7 @@ PartView part_view(lbm_ctx* ctx)
     v.pkf = ctx->pkf;
     v.pending = ctx->pending;
     v.ismask = ctx->ismask;
+    v.step_id = ctx->step_id;
     return v;
 }
 
@@ -579,7 +584,9 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
         CS(dev_alloc(ctx, &ctx->cnt, sizeof(Counters)));
         CS(dev_alloc(ctx, &ctx->pairs, sizeof(unsigned long long) * PAIR_CAP));
         CS(dev_alloc(ctx, &ctx->ismask, sizeof(unsigned) * (size_t)ctx->g.N));
-        CS(dev_alloc(ctx, (char**)&ctx->bs_scratch, (size_t)ctx->kt->compute_bytes * 6 * (size_t)ctx->g.N));
+        const size_t rec = ctx->precision == LBM_FP64 ? 6 * sizeof(double) : 8 * sizeof(float);
+        CS(dev_alloc(ctx, (char**)&ctx->bs_scratch, rec * (size_t)ctx->g.N));
+        CK(cudaMemsetAsync(ctx->bs_scratch, 0, rec * (size_t)ctx->g.N, ctx->stream));
         CK(prepare_particle_kernels(PAIR_CAP));
     }
     // Cell grid for contact and neighbour searches: cells at least 2 r_max + gap + 4 wide.

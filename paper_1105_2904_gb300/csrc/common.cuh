@@ -177,6 +177,7 @@ struct PartView {
     // Per-site mask of pull directions whose source is an IS site of the site's own owner
     // (bit i), and bit 31 when some source is an IS site of another particle.
     const unsigned* ismask;
+    const unsigned* step_id;  // advanced once per step by the particle phase
 };
 
 constexpr unsigned MASK_OTHER = 1u << 31;

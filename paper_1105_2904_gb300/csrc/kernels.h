@@ -18,7 +18,9 @@ struct SweepArgs {
     PartView pv;               // tag == nullptr: no particles
     const void* stash_in;      // [N] compute type (double / float): site density (deviation)
     void* stash_out;           // [N]
-    void* bs_scratch;          // [N][6] per-site dP, dL at BS sites (double in FP64 mode, else float)
+    void* bs_scratch;          // per-site dP, dL at BS sites: FP64 mode [N][6] doubles; FP32 modes
+                               // [N][8] floats (dP, dL, owner tag bits, step id bits: one 32-byte
+                               // sector)
     double omega, pre, F[3];   // 1/tau, 1 - 1/(2 tau), body force
     float omega_f, pre_f, F_f[3];  // the same in FP32 (reduced-storage sweeps)
 };
@@ -114,11 +116,12 @@ struct ParticleArgs {
     double* un;         // [np][3] velocity during the contact step
     double* acc;        // [np][6]
     double* force;      // [np][6] -dP, -dL of the last step
-    const void* bs_scratch;  // per-site dP, dL at BS sites ([N][6], double or float)
+    const void* bs_scratch;  // per-site dP, dL at BS sites (layout as in SweepArgs)
     int scratch_f64;         // 1: bs_scratch holds doubles (FP64 mode)
     Counters* cnt;
     int* status;        // device status word (first fault wins)
     int* pending;
+    unsigned* step_id;  // stamps the sweep's per-site records; advanced by the move kernel
     CellGrid cg;
     int* cell_of;       // [np]
     int* cell_count;    // [total]

@@ -55,7 +55,9 @@ __global__ void k_reduce_ordered(const ParticleArgs a)
 
 // FP32 modes: one block per particle. Thread t sums entries t, t + T, ... in FP32 (loads
 // of four entries in flight), then a fixed tree combines the threads (deterministic), and
-// the total is stored in FP64.
+// the total is stored in FP64. Each site's 32-byte record holds the id of the particle that
+// owned it as BS in the sweep and the step it was written in, so no owner-map read is
+// needed.
 constexpr int RT = 128;
 __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a)
 {
@@ -64,7 +66,8 @@ __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a)
     const PConst pc = a.pc[p];
     const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
     const unsigned code = (CLS_BS << 30) | (unsigned)p;
-    const float* sc = (const float*)a.bs_scratch;
+    const float4* sc = (const float4*)a.bs_scratch;
+    const unsigned sid = *a.step_id;
     float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int e0 = threadIdx.x; e0 < pc.n_bs; e0 += 4 * RT) {
         unsigned site[4];
@@ -78,19 +81,24 @@ __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a)
                 ok[u] = site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site[u]);
             }
         }
-        unsigned t[4];
+        float4 v0[4], v1[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) t[u] = ok[u] ? a.tag[site[u]] : 0u;
-        float v[4][6];
+        for (int u = 0; u < 4; ++u) {
+            v0[u] = ok[u] ? sc[(size_t)site[u] * 2] : make_float4(0.f, 0.f, 0.f, 0.f);
+            v1[u] = ok[u] ? sc[(size_t)site[u] * 2 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // the record carries the owner that wrote it and the step: only records written
+        // this step by this particle's own BS sites count
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int q = 0; q < 6; ++q) v[u][q] = ok[u] ? sc[(size_t)site[u] * 6 + q] : 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (ok[u] && t[u] == code)
-#pragma unroll
-                for (int q = 0; q < 6; ++q) s[q] += v[u][q];
+            if (ok[u] && __float_as_uint(v1[u].z) == code && __float_as_uint(v1[u].w) == sid) {
+                s[0] += v0[u].x;
+                s[1] += v0[u].y;
+                s[2] += v0[u].z;
+                s[3] += v0[u].w;
+                s[4] += v1[u].x;
+                s[5] += v1[u].y;
+            }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -310,7 +318,10 @@ __global__ void k_move(const ParticleArgs a)
 {
     const int D = a.lattice == 0 ? 2 : 3;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0) *a.pending = 1;
+    if (p == 0) {
+        *a.pending = 1;
+        *a.step_id += 1u;
+    }
     if (p < a.np) {
         const PConst pc = a.pc[p];
         double* u = &a.un[(size_t)p * 3];

