@@ -434,31 +434,16 @@ __global__ void k_update_masks(const MaskArgs a)
     }
 }
 
+// Everything a site does after its populations are pulled: the pending IS imposition,
+// the collision, the BS transfer and its per-site record, the stores and the IS density.
 template <class L, typename S, bool WALLS, bool PART>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
+__device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int z, unsigned idx, bool valid,
+                                           const Nbr& n, typename Store<S>::C f[], unsigned tagx, unsigned mask)
 {
     using St = Store<S>;
     using C = typename St::C;
     constexpr int Q = L::Q;
     const Geom& g = a.g;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const unsigned row = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx;
-    const int xr = blockIdx.x * SWEEP_THREADS + threadIdx.x;
-    const bool valid = xr < g.nx;
-    const int x = valid ? xr : g.nx - 1;
-    const unsigned idx = row + (unsigned)x;
-    const size_t N = g.N;
-    const Nbr n = neighbours<WALLS>(g, x, y, z);
-
-    // Owner tag and IS-source mask are loaded with the populations (no dependent round trip).
-    unsigned tagx = TAG_FLUID, mask = 0;
-    if constexpr (PART) {
-        tagx = a.pv.tag[idx];
-        mask = a.pv.ismask[idx];
-    }
-    C f[Q];
-    pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
-
     if constexpr (PART) {
         if (tagx != TAG_FLUID && *a.pv.pending) {
             const unsigned m = mask;
@@ -556,6 +541,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
 
     if (!valid) return;
     S* __restrict__ fout = (S*)a.fout;
+    const size_t N = g.N;
     // Post-collision density of IS sites, for the IS imposition pulled next step: the sum
     // of the values as stored.
     const bool isis = PART && (tagx >> 30) == CLS_IS;
@@ -567,6 +553,31 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
         if (isis) dens += St::load(s, (C)L::w(i));
     });
     if (isis) ((C*)a.stash_out)[idx] = dens;
+}
+
+
+template <class L, typename S, bool WALLS, bool PART>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
+{
+    using C = typename Store<S>::C;
+    constexpr int Q = L::Q;
+    const Geom& g = a.g;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned row = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx;
+    const int xr = blockIdx.x * SWEEP_THREADS + threadIdx.x;
+    const bool valid = xr < g.nx;
+    const int x = valid ? xr : g.nx - 1;
+    const unsigned idx = row + (unsigned)x;
+    const Nbr n = neighbours<WALLS>(g, x, y, z);
+    // Owner tag and IS-source mask are loaded with the populations (no dependent round trip).
+    unsigned tagx = TAG_FLUID, mask = 0;
+    if constexpr (PART) {
+        tagx = a.pv.tag[idx];
+        mask = a.pv.ismask[idx];
+    }
+    C f[Q];
+    pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
+    sweep_site<L, S, WALLS, PART>(a, x, y, z, idx, valid, n, f, tagx, mask);
 }
 
 template <class L, typename S, bool WALLS>
@@ -726,16 +737,22 @@ __global__ void k_stash_fix(const StashFixArgs a)
 }
 
 // ---- launchers --------------------------------------------------------------------------
+template <class L, typename S, bool WALLS, bool PART>
+void launch_sweep_v(const SweepArgs& a, cudaStream_t s)
+{
+    const dim3 grid((a.g.nx + SWEEP_THREADS - 1) / SWEEP_THREADS, a.g.ny, a.g.nz);
+    k_sweep<L, S, WALLS, PART><<<grid, SWEEP_THREADS, 0, s>>>(a);
+}
+
 template <class L, typename S>
 void launch_sweep_l(const SweepArgs& a, cudaStream_t s)
 {
-    const dim3 grid((a.g.nx + SWEEP_THREADS - 1) / SWEEP_THREADS, a.g.ny, a.g.nz);
     const bool walls = a.g.wall[0] || a.g.wall[1] || a.g.wall[2];
     const bool part = a.pv.tag != nullptr;
-    if (walls && part) k_sweep<L, S, true, true><<<grid, SWEEP_THREADS, 0, s>>>(a);
-    else if (walls) k_sweep<L, S, true, false><<<grid, SWEEP_THREADS, 0, s>>>(a);
-    else if (part) k_sweep<L, S, false, true><<<grid, SWEEP_THREADS, 0, s>>>(a);
-    else k_sweep<L, S, false, false><<<grid, SWEEP_THREADS, 0, s>>>(a);
+    if (walls && part) launch_sweep_v<L, S, true, true>(a, s);
+    else if (walls) launch_sweep_v<L, S, true, false>(a, s);
+    else if (part) launch_sweep_v<L, S, false, true>(a, s);
+    else launch_sweep_v<L, S, false, false>(a, s);
 }
 
 template <typename S>
