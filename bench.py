@@ -64,6 +64,30 @@ def dist_setup():
     return world, rank, local
 
 
+def reduce_max(value):
+    """Maximum of a float over all ranks (identity without a process group). Works with the
+    nccl backend (tensor on the current CUDA device) and with gloo (CPU tensor)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(sites, steps, ms_local):
+    """Whole-job MLUPS of independent replicas: every rank advanced `sites` sites by `steps`
+    steps; the job time is the slowest rank's."""
+    import torch.distributed as dist
+
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    ms = reduce_max(ms_local)
+    return sites * steps * world / (ms / 1e3) / 1e6, ms
+
+
 def source_sha():
     h = hashlib.sha256()
     for f in ("sweep.cuh", "common.cuh", "kernels.h"):
@@ -260,13 +284,8 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     sim.synchronize()   # raises on a device fault recorded during the timed steps
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     info = sim.info()
-    value = N * args.steps * world / (ms / 1e3) / 1e6
+    value, ms = aggregate_throughput(N, args.steps, e0.elapsed_time(e1))
 
     # Roofline of the dominant kernel (the sweep): per-launch duration with CUDA events.
     prof = sim.profile(min(args.steps, 50))
@@ -301,10 +320,7 @@ def run_ours(args):
             lbmp.lbm_get_particles(s2.h, n, host)
         dt = time.perf_counter() - t
         s2.close()
-        if world > 1:
-            tt = torch.tensor([dt], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = reduce_max(dt)
         h2d = (c.nbytes + r.nbytes + d.nbytes + v.nbytes) / args.steps
         e2e = {"value": N * args.steps * world / dt / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(5 * n * 3 * 8),

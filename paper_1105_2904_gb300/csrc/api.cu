@@ -65,6 +65,9 @@ struct lbm_ctx {
     int *changed = nullptr, *restamp = nullptr, *restamp_flag = nullptr;
 
     double* staging = nullptr;
+    void* pinned = nullptr;  // page-locked host staging for particle read-backs
+    size_t pinned_bytes = 0;
+    double* pout = nullptr;  // [15][np] packed particle state on the device
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int launches_per_step = 0;
     long long steps = 0;
@@ -497,25 +500,69 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
                 c.ext[a] = ctx->grav[a] * (1.0 - inv_rho) + (ctx->bfp ? ctx->F[a] * inv_rho : 0.0);
         }
     }
-    // Hard-core particles may not overlap (Sec. 2.3).
+    // Hard-core particles may not overlap (Sec. 2.3). Candidates come from a uniform grid of
+    // cells at least 2 r_max wide, so each new particle is tested against 27 cells.
     std::vector<double> allx(ctx->h_x);
     allx.insert(allx.end(), xs.begin(), xs.end());
     std::vector<double> allr;
     for (auto& c : ctx->h_pc) allr.push_back(c.r);
     for (auto& c : pc) allr.push_back(c.r);
     const int tot = ctx->np + n;
-    for (int i = ctx->np; i < tot; ++i)
-        for (int j = 0; j < i; ++j) {
-            double d2 = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                const double d = min_image_h(allx[3 * (size_t)i + a] - allx[3 * (size_t)j + a], axis_n(ctx, a),
-                                             a < D && !ctx->g.wall[a]);
-                d2 += d * d;
-            }
-            const double R = allr[i] + allr[j];
-            if (d2 < R * R) return fail(ctx, LBM_E_OVERLAP, "particles " + std::to_string(j) + " and " +
-                                                                std::to_string(i) + " overlap");
+    {
+        double rmax_all = 0.0;
+        for (double rr : allr) rmax_all = std::max(rmax_all, rr);
+        int nc[3];
+        double cs[3];
+        for (int a = 0; a < 3; ++a) {
+            const int na = axis_n(ctx, a);
+            nc[a] = a < D ? std::max(1, std::min(1024, (int)std::floor((double)na / (2.0 * rmax_all + 1e-9)))) : 1;
+            cs[a] = (double)na / nc[a];
         }
+        auto cell_of = [&](int i, int a) {
+            const int na = axis_n(ctx, a);
+            double v = allx[3 * (size_t)i + a];
+            if (a >= D) return 0;
+            v = ctx->g.wall[a] ? v + 0.5 : v - (double)na * std::floor(v / (double)na);
+            int c = (int)std::floor(v / cs[a]);
+            return std::min(std::max(c, 0), nc[a] - 1);
+        };
+        std::vector<std::vector<int>> cells((size_t)nc[0] * nc[1] * nc[2]);
+        for (int i = 0; i < tot; ++i)
+            cells[((size_t)cell_of(i, 2) * nc[1] + cell_of(i, 1)) * nc[0] + cell_of(i, 0)].push_back(i);
+        for (int i = ctx->np; i < tot; ++i) {
+            const int ci[3] = {cell_of(i, 0), cell_of(i, 1), cell_of(i, 2)};
+            std::vector<size_t> seen;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int cc[3] = {ci[0] + dx, ci[1] + dy, ci[2] + dz};
+                        bool skip = false;
+                        for (int a = 0; a < 3; ++a) {
+                            if (cc[a] < 0 || cc[a] >= nc[a]) {
+                                if (ctx->g.wall[a] || a >= D) skip = true;
+                                cc[a] = (cc[a] + nc[a]) % nc[a];
+                            }
+                        }
+                        if (skip) continue;
+                        const size_t cid = ((size_t)cc[2] * nc[1] + cc[1]) * nc[0] + cc[0];
+                        if (std::find(seen.begin(), seen.end(), cid) != seen.end()) continue;
+                        seen.push_back(cid);
+                        for (int j : cells[cid]) {
+                            if (j >= i) continue;
+                            double d2 = 0.0;
+                            for (int a = 0; a < 3; ++a) {
+                                const double d = min_image_h(allx[3 * (size_t)i + a] - allx[3 * (size_t)j + a],
+                                                             axis_n(ctx, a), a < D && !ctx->g.wall[a]);
+                                d2 += d * d;
+                            }
+                            const double R = allr[i] + allr[j];
+                            if (d2 < R * R)
+                                return fail(ctx, LBM_E_OVERLAP, "particles " + std::to_string(j) + " and " +
+                                                                    std::to_string(i) + " overlap");
+                        }
+                    }
+        }
+    }
     // Site classification of each new particle (independent, spread over host threads).
     std::vector<std::vector<int>> tm(n);
     {
@@ -560,7 +607,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
                     (void*)ctx->acc, (void*)ctx->force, (void*)ctx->Kold, (void*)ctx->cell_of,
                     (void*)ctx->cell_count, (void*)ctx->cell_start, (void*)ctx->cell_cursor,
                     (void*)ctx->cell_items, (void*)ctx->changed, (void*)ctx->restamp,
-                    (void*)ctx->restamp_flag})
+                    (void*)ctx->restamp_flag, (void*)ctx->pout})
         release(p);
     const size_t np = (size_t)ctx->np;
     CS(dev_alloc(ctx, &ctx->pk, sizeof(PKern) * np));
@@ -577,6 +624,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CS(dev_alloc(ctx, &ctx->changed, sizeof(int) * np));
     CS(dev_alloc(ctx, &ctx->restamp, sizeof(int) * np));
     CS(dev_alloc(ctx, &ctx->restamp_flag, sizeof(int) * np));
+    CS(dev_alloc(ctx, &ctx->pout, sizeof(double) * 15 * np));
     if (!ctx->tag) {
         CS(dev_alloc(ctx, &ctx->tag, sizeof(unsigned) * (size_t)ctx->g.N));
         CS(dev_alloc(ctx, &ctx->stash[0], (size_t)ctx->kt->compute_bytes * ctx->g.N));
@@ -769,21 +817,26 @@ lbm_status lbm_set_distributions(lbm_ctx* ctx, const double* f)
 lbm_status lbm_get_particles(lbm_ctx* ctx, double* x, double* u, double* omega, double* force, double* torque)
 {
     if (!ctx) return LBM_E_INVALID;
-    CS(sync_status(ctx));
     const size_t np = (size_t)ctx->np;
-    if (np == 0) return LBM_OK;
-    std::vector<PKern> pk(np);
-    std::vector<double> fo(6 * np);
-    CK(cudaMemcpy(pk.data(), ctx->pk, sizeof(PKern) * np, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(fo.data(), ctx->force, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost));
-    if (x) CK(cudaMemcpy(x, ctx->x, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost));
-    for (size_t p = 0; p < np; ++p)
-        for (int k = 0; k < 3; ++k) {
-            if (u) u[3 * p + k] = pk[p].u[k];
-            if (omega) omega[3 * p + k] = pk[p].om[k];
-            if (force) force[3 * p + k] = fo[6 * p + k];
-            if (torque) torque[3 * p + k] = fo[6 * p + 3 + k];
-        }
+    if (np == 0) return sync_status(ctx);
+    // One kernel packs x, u, omega, force, torque into the staging buffer; one copy brings
+    // them to a pinned host buffer.
+    const size_t bytes = sizeof(double) * 15 * np;
+    if (ctx->pinned_bytes < bytes) {
+        if (ctx->pinned) cudaFreeHost(ctx->pinned);
+        ctx->pinned = nullptr;
+        ctx->pinned_bytes = 0;
+        CK(cudaMallocHost(&ctx->pinned, bytes));
+        ctx->pinned_bytes = bytes;
+    }
+    launch_pack_particles(particle_args(ctx), ctx->pout, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->pinned, ctx->pout, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CS(sync_status(ctx));
+    const double* h = (const double*)ctx->pinned;
+    double* outs[5] = {x, u, omega, force, torque};
+    for (int k = 0; k < 5; ++k)
+        if (outs[k]) std::memcpy(outs[k], h + (size_t)k * 3 * np, sizeof(double) * 3 * np);
     return LBM_OK;
 }
 
@@ -826,6 +879,7 @@ void lbm_destroy(lbm_ctx* ctx)
     for (int c = 0; c < 2; ++c)
         if (ctx->gexec[c]) cudaGraphExecDestroy(ctx->gexec[c]);
     for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

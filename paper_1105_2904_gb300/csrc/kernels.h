@@ -141,6 +141,8 @@ struct ParticleArgs {
 int launch_particle_phase(const ParticleArgs& a, cudaStream_t s);
 // Stamps every particle's site set into a cleared owner map (after lbm_add_particles).
 void launch_stamp_all(const ParticleArgs& a, cudaStream_t s);
+// Packs x, u, omega, force, torque of every particle into out (five [np][3] blocks).
+void launch_pack_particles(const ParticleArgs& a, double* out, cudaStream_t s);
 // Opts the contact kernel into the shared memory its pair list needs.
 cudaError_t prepare_particle_kernels(int pair_cap);
 

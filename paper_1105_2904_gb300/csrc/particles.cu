@@ -455,6 +455,21 @@ __global__ void k_stamp_all(const ParticleArgs a)
 
 int mark_grid() { return 304; }
 
+// x, u, omega, -dP, -dL of every particle as five [np][3] blocks of out.
+__global__ void k_pack_particles(const ParticleArgs a, double* out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const size_t np = (size_t)a.np;
+    for (int k = 0; k < 3; ++k) {
+        out[0 * 3 * np + (size_t)p * 3 + k] = a.x[(size_t)p * 3 + k];
+        out[1 * 3 * np + (size_t)p * 3 + k] = a.pk[p].u[k];
+        out[2 * 3 * np + (size_t)p * 3 + k] = a.pk[p].om[k];
+        out[3 * 3 * np + (size_t)p * 3 + k] = a.force[(size_t)p * 6 + k];
+        out[4 * 3 * np + (size_t)p * 3 + k] = a.force[(size_t)p * 6 + 3 + k];
+    }
+}
+
 }  // namespace
 
 int launch_particle_phase(const ParticleArgs& a, cudaStream_t s)
@@ -482,6 +497,11 @@ int launch_particle_phase(const ParticleArgs& a, cudaStream_t s)
     k_mark_stamp<<<mark_grid(), 256, 0, s>>>(a);
     launches += 9;
     return launches;
+}
+
+void launch_pack_particles(const ParticleArgs& a, double* out, cudaStream_t s)
+{
+    k_pack_particles<<<(a.np + PT - 1) / PT, PT, 0, s>>>(a, out);
 }
 
 void launch_stamp_all(const ParticleArgs& a, cudaStream_t s)
