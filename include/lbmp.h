@@ -90,6 +90,20 @@ lbm_status lbm_configure(lbm_ctx* ctx, int precision, const int faces[6],
                          const double particle_gravity[3], double contact_gap,
                          int body_force_on_particles, void* cuda_stream);
 
+/* Moves wall face `face` (0..5 = -x,+x,-y,+y,-z,+z) in its own plane with velocity u
+ * (xyz; u[face/2] must be 0). The paper drives its shear and channel flows through
+ * velocity-imposed walls (Secs. 3.1-3.2) without stating the mechanism; here a population
+ * that bounces off a moving wall gains the wall momentum -6 w_i (c_i . u_w) at reference
+ * density 1 (halfway bounce-back). A move crossing two walls takes the wall of its lowest
+ * axis. The velocity applies from the streaming of the next step on (lbm_get_* still see the
+ * last step streamed with the velocity it was taken with); the first step after creation or
+ * lbm_set_distributions pulls the given populations as they are. Allowed at any time
+ * between steps (the stream is synchronised); lbm_configure clears the velocity of faces it
+ * makes periodic.
+ * Errors: LBM_E_INVALID (face out of range or periodic, u NULL, not finite, or with a
+ * normal component); LBM_E_CUDA. */
+lbm_status lbm_set_wall_velocity(lbm_ctx* ctx, int face, const double u[3]);
+
 /* Adds n rigid spheres (disks for D2Q9) (Sec. 2.2: centre x_p, radius r_p, mass and
  * moment of inertia from the density). centers, velocities and omegas are n*3 (xyz);
  * radii and densities are n. densities are particle/fluid density ratios; +INFINITY makes

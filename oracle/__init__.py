@@ -62,6 +62,7 @@ def _lib():
             lib.osim_destroy.argtypes = [P]
             lib.osim_set_walls.argtypes = [P, I]
             lib.osim_set_particle_options.argtypes = [P, D, ctypes.c_double, ctypes.c_int]
+            lib.osim_set_wall_velocity.argtypes = [P, ctypes.c_int, D]
             lib.osim_add_particles.argtypes = [P, ctypes.c_int, D, D, D, D, D]
             lib.osim_step.argtypes = [P, ctypes.c_int]
             lib.osim_get_f.argtypes = [P, D]
@@ -93,7 +94,8 @@ class OracleSim:
     """One FP64 CPU simulation (lattice 0 = D2Q9 with nz = 1, 1 = D3Q19)."""
 
     def __init__(self, lattice, nx, ny, nz, tau, body_force=(0.0, 0.0, 0.0),
-                 walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False):
+                 walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False,
+                 wall_velocity=None):
         self.lib = _lib()
         self.lattice = lattice
         self.Q = 9 if lattice == D2Q9 else 19
@@ -108,6 +110,13 @@ class OracleSim:
             raise ValueError("oracle: walls must be set before particles")
         g = _f64(gravity, (3,))
         self.lib.osim_set_particle_options(self.h, _dp(g), float(gap), int(bool(body_force_on_particles)))
+        for face, u in (wall_velocity or {}).items():
+            self.set_wall_velocity(face, u)
+
+    def set_wall_velocity(self, face, u):
+        uu = _f64(u, (3,))
+        if self.lib.osim_set_wall_velocity(self.h, int(face), _dp(uu)) != 0:
+            raise ValueError("oracle: face %d is not a wall, or the velocity is not tangential" % face)
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -37,6 +37,8 @@
  *      post-acceleration velocities; candidate pairs processed once in (i,j) order, each
  *      reflected only if still approaching.
  *   R12 mass and inertia: continuum values of a sphere (3D) or disk (2D).
+ *   R15 moving walls (velocity-imposed boundaries of Secs. 3.1-3.2, mechanism not given):
+ *      halfway bounce-back with the wall-momentum term -6 w_i (c_i . u_w), density 1.
  *
  * Distribution layout f[i][z][y][x]; lattice velocity order below.
  * Compile with -ffp-contract=off: the arithmetic is meant to be evaluated exactly as written.
@@ -78,6 +80,7 @@ struct osim {
     long N;
     double tau, omega, F[3];
     int walls[3];
+    double wall_u[6][3]; /* velocity of each face (-x,+x,-y,+y,-z,+z); tangential */
     double g[3], gap;
     int bfp;
     double* f;    /* state at the start of a step (pre-collision), [Q][N] */
@@ -321,6 +324,14 @@ int osim_set_walls(osim* s, const int walls[3])
     if (s->np > 0) return -1;
     for (int k = 0; k < 3; k++) s->walls[k] = walls[k] ? 1 : 0;
     if (s->L.D == 2) s->walls[2] = 0;
+    return 0;
+}
+
+int osim_set_wall_velocity(osim* s, int face, const double u[3])
+{
+    if (face < 0 || face > 5 || !s->walls[face / 2]) return -1;
+    if (u[face / 2] != 0.0) return -2; /* the wall plane does not move along its normal */
+    for (int k = 0; k < 3; k++) s->wall_u[face][k] = (s->L.D == 2 && k == 2) ? 0.0 : u[k];
     return 0;
 }
 
@@ -575,20 +586,27 @@ static void step_once(osim* s)
                 long src = ((long)z * s->ny + y) * s->nx + x;
                 int pos[3] = {x, y, z}, n3[3] = {s->nx, s->ny, s->nz};
                 for (int i = 0; i < Q; i++) {
-                    int t[3], bounce = 0;
+                    int t[3], bounce = 0, face = -1;
                     for (int k = 0; k < 3; k++) {
                         t[k] = pos[k] + L->c[i][k];
                         if (t[k] < 0 || t[k] >= n3[k]) {
-                            if (s->walls[k])
+                            if (s->walls[k]) {
                                 bounce = 1;
-                            else
+                                if (face < 0) face = 2 * k + (t[k] >= n3[k] ? 1 : 0);
+                            } else {
                                 t[k] = (t[k] + n3[k]) % n3[k];
+                            }
                         }
                     }
                     double v = s->fp[(long)i * N + src];
-                    if (bounce)
-                        s->f[(long)L->opp[i] * N + src] = v;
-                    else
+                    if (bounce) {
+                        /* R15 moving wall (halfway bounce-back with the momentum of a wall moving
+                         * at u_w, reference density 1): f_opp(i) = f*_i - 6 w_i (c_i . u_w); a move
+                         * crossing two walls takes the wall of its lowest axis. */
+                        const double* uw = s->wall_u[face];
+                        const double cuw = L->c[i][0] * uw[0] + L->c[i][1] * uw[1] + L->c[i][2] * uw[2];
+                        s->f[(long)L->opp[i] * N + src] = v - 6.0 * L->w[i] * cuw;
+                    } else
                         s->f[(long)i * N + ((long)t[2] * s->ny + t[1]) * s->nx + t[0]] = v;
                 }
             }

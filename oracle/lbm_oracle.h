@@ -29,6 +29,9 @@ void osim_destroy(osim* s);
 
 /* walls[k] = 1: no-slip halfway bounce-back walls at both ends of axis k, 0: periodic. */
 int osim_set_walls(osim* s, const int walls[3]);
+/* Tangential velocity of a wall face (0..5 = -x,+x,-y,+y,-z,+z); the face must be a wall.
+ * Returns 0, or <0 if the face is periodic or u has a normal component. */
+int osim_set_wall_velocity(osim* s, int face, const double u[3]);
 /* gravity on particles (net buoyant), contact gap, whether F also acts on particles (F/rho_p). */
 void osim_set_particle_options(osim* s, const double g[3], double gap, int body_force_on_particles);
 

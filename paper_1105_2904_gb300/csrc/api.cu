@@ -28,6 +28,9 @@ struct lbm_ctx {
     int precision = LBM_FP32;
     const KernelTable* kt = nullptr;
     double grav[3] = {0, 0, 0};
+    double uw[6][3] = {};      // tangential velocity of each wall face (host copy)
+    bool moving_walls = false; // set once a face is given a velocity; never cleared
+    WallVel* wv = nullptr;     // device: [0] velocities of the pending streaming, [1] current
     double gap = 0.0;
     int bfp = 0;
     cudaStream_t stream = nullptr;
@@ -130,6 +133,17 @@ const KernelTable* table_for(int precision)
 
 int lat_c(int lattice, int i, int k) { return lattice == 0 ? D2Q9::c(i, k) : D3Q19::c(i, k); }
 
+WallVel wall_vel(const lbm_ctx* ctx)
+{
+    WallVel w{};
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 3; ++k) {
+            w.u[f][k] = ctx->uw[f][k];
+            w.uf[f][k] = (float)ctx->uw[f][k];
+        }
+    return w;
+}
+
 lbm_status ensure_alloc(lbm_ctx* ctx)
 {
     if (ctx->allocated) return LBM_OK;
@@ -141,10 +155,15 @@ lbm_status ensure_alloc(lbm_ctx* ctx)
     CS(dev_alloc(ctx, &ctx->status, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->pending, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->step_id, sizeof(unsigned)));
+    CS(dev_alloc(ctx, &ctx->wv, 2 * sizeof(WallVel)));
     CS(dev_alloc(ctx, &ctx->staging, STAGING_BYTES));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(ctx->pending, 0, sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(ctx->step_id, 0, sizeof(unsigned), ctx->stream));
+    {
+        const WallVel w[2] = {wall_vel(ctx), wall_vel(ctx)};
+        CK(cudaMemcpyAsync(ctx->wv, w, sizeof(w), cudaMemcpyHostToDevice, ctx->stream));
+    }
     ctx->kt->fill_rest(ctx->lattice, ctx->f[0], ctx->g.N, ctx->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
@@ -282,6 +301,13 @@ PartView part_view(lbm_ctx* ctx)
     return v;
 }
 
+template <class A>
+void wall_args(const lbm_ctx* ctx, A& a)
+{
+    a.moving_walls = ctx->moving_walls ? 1 : 0;
+    a.uw = ctx->wv;
+}
+
 // One time step on ctx->stream, reading buffer c and writing buffer 1 - c. With ev != nullptr
 // CUDA events are recorded before the sweep, after it, and after the particle phase.
 int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
@@ -301,6 +327,7 @@ int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
     a.omega_f = (float)a.omega;
     a.pre_f = (float)a.pre;
     for (int k = 0; k < 3; ++k) a.F_f[k] = (float)ctx->F[k];
+    wall_args(ctx, a);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
     ctx->kt->sweep(a, ctx->stream);
     if (ev) cudaEventRecord(ev[1], ctx->stream);
@@ -320,6 +347,10 @@ int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
         ctx->kt->stash_fix(s, ctx->stream);
         ctx->kt->update_masks(mask_args(ctx, true), ctx->stream);
         launches += 2;
+    }
+    if (ctx->moving_walls) {
+        launch_wall_advance(ctx->wv, ctx->pending, ctx->stream);
+        launches += 1;
     }
     if (ev) cudaEventRecord(ev[2], ctx->stream);
     return launches;
@@ -422,10 +453,43 @@ lbm_status lbm_configure(lbm_ctx* ctx, int precision, const int faces[6], const 
     if (ctx->D == 2) ctx->grav[2] = 0.0;
     ctx->gap = contact_gap;
     ctx->bfp = body_force_on_particles ? 1 : 0;
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 3; ++k)
+            if (!walls[f / 2]) ctx->uw[f][k] = 0.0;
     if (cuda_stream) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         ctx->stream = (cudaStream_t)cuda_stream;
         ctx->own_stream = false;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_velocity(lbm_ctx* ctx, int face, const double u[3])
+{
+    if (!ctx) return LBM_E_INVALID;
+    if (face < 0 || face > 5 || !u) return fail(ctx, LBM_E_INVALID, "face must be 0..5 and u non-null");
+    if (!ctx->g.wall[face / 2]) return fail(ctx, LBM_E_INVALID, "the face is periodic, not a wall");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(u[k])) return fail(ctx, LBM_E_INVALID, "wall velocity must be finite");
+    if (u[face / 2] != 0.0) return fail(ctx, LBM_E_INVALID, "a wall moves only in its own plane");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 3; ++k) ctx->uw[face][k] = (ctx->D == 2 && k == 2) ? 0.0 : u[k];
+    bool moving = false;
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 3; ++k) moving = moving || ctx->uw[f][k] != 0.0;
+    if (ctx->allocated) {
+        // Only the current set changes: the streaming still pending (the values the next pull
+        // completes) keeps the velocities it was taken with.
+        const WallVel w = wall_vel(ctx);
+        CK(cudaMemcpy(ctx->wv + 1, &w, sizeof(w), cudaMemcpyHostToDevice));
+    }
+    if (moving && !ctx->moving_walls) {
+        ctx->moving_walls = true;  // the step graphs gain the wall term and its advance
+        for (int c = 0; c < 2; ++c)
+            if (ctx->gexec[c]) {
+                cudaGraphExecDestroy(ctx->gexec[c]);
+                ctx->gexec[c] = nullptr;
+            }
     }
     return LBM_OK;
 }
@@ -744,6 +808,7 @@ static lbm_status materialize(lbm_ctx* ctx, int mode, double* out_a, double* out
         a.pv = part_view(ctx);
         a.stash_in = ctx->stash[ctx->cur];
         for (int k = 0; k < 3; ++k) a.F[k] = ctx->F[k];
+        wall_args(ctx, a);
         a.s0 = (unsigned)s0;
         a.count = (unsigned)cnt;
         a.mode = mode;

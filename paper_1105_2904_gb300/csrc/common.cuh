@@ -162,6 +162,12 @@ struct Counters {
     int pad;
 };
 
+// Tangential velocity of each wall face (-x,+x,-y,+y,-z,+z), in FP64 and FP32.
+struct WallVel {
+    double u[6][3];
+    float uf[6][3];
+};
+
 struct Geom {
     int nx, ny, nz;
     int wall[3];     // 1 = halfway bounce-back walls on both ends of the axis

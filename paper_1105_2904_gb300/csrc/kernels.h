@@ -23,6 +23,8 @@ struct SweepArgs {
                                // sector)
     double omega, pre, F[3];   // 1/tau, 1 - 1/(2 tau), body force
     float omega_f, pre_f, F_f[3];  // the same in FP32 (reduced-storage sweeps)
+    int moving_walls;          // 1: wall faces may move (uw is read)
+    const WallVel* uw;         // wall velocities of the streaming that the pull completes
 };
 
 struct MaterializeArgs {
@@ -32,6 +34,8 @@ struct MaterializeArgs {
     PartView pv;
     const void* stash_in;
     double F[3];
+    int moving_walls;
+    const WallVel* uw;
     unsigned s0, count;        // site range [s0, s0 + count)
     int mode;                  // 0: rho[count], u[count][3]; 1: f[Q][count]
     double* out0;
@@ -141,6 +145,9 @@ struct ParticleArgs {
 int launch_particle_phase(const ParticleArgs& a, cudaStream_t s);
 // Stamps every particle's site set into a cleared owner map (after lbm_add_particles).
 void launch_stamp_all(const ParticleArgs& a, cudaStream_t s);
+// After a sweep with moving walls: the current wall velocities become those of the streaming
+// that the next pull completes (wv[0] <- wv[1]), and the pulled values await streaming.
+void launch_wall_advance(WallVel* wv, int* pending, cudaStream_t s);
 // Packs x, u, omega, force, torque of every particle into out (five [np][3] blocks).
 void launch_pack_particles(const ParticleArgs& a, double* out, cudaStream_t s);
 // Opts the contact kernel into the shared memory its pair list needs.

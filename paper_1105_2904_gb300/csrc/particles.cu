@@ -504,6 +504,21 @@ void launch_pack_particles(const ParticleArgs& a, double* out, cudaStream_t s)
     k_pack_particles<<<(a.np + PT - 1) / PT, PT, 0, s>>>(a, out);
 }
 
+__global__ void k_wall_advance(WallVel* wv, int* pending)
+{
+    const int t = threadIdx.x;
+    if (t < 18) {
+        wv[0].u[t / 3][t % 3] = wv[1].u[t / 3][t % 3];
+        wv[0].uf[t / 3][t % 3] = wv[1].uf[t / 3][t % 3];
+    }
+    if (t == 0) *pending = 1;
+}
+
+void launch_wall_advance(WallVel* wv, int* pending, cudaStream_t s)
+{
+    k_wall_advance<<<1, 32, 0, s>>>(wv, pending);
+}
+
 void launch_stamp_all(const ParticleArgs& a, cudaStream_t s)
 {
     k_stamp_all<<<mark_grid(), 256, 0, s>>>(a);

@@ -245,6 +245,41 @@ __device__ __forceinline__ void pull_source(const Geom& g, const Nbr& n, int x, 
     }
 }
 
+// Face crossed by the move x + c_d (lowest axis first), or -1 if it stays in the domain.
+template <class L, int d>
+__device__ __forceinline__ int out_face(const Nbr& n)
+{
+    constexpr int cx = L::c(d, 0), cy = L::c(d, 1), cz = L::c(d, 2);
+    if (cx > 0 && n.bxp) return 1;
+    if (cx < 0 && n.bxm) return 0;
+    if (cy > 0 && n.byp) return 3;
+    if (cy < 0 && n.bym) return 2;
+    if (cz > 0 && n.bzp) return 5;
+    if (cz < 0 && n.bzm) return 4;
+    return -1;
+}
+
+// Momentum of a moving wall given to a bounced population (halfway bounce-back at a wall
+// moving with u_w, reference density 1): the population pulled in direction i left x in
+// direction d = opp(i) and returns as f*_d - 6 w_d (c_d . u_w). The same term applies to
+// the deviation g = f - w, since w_i = w_d.
+template <class L, typename C, bool WALLS>
+__device__ __forceinline__ void wall_momentum(const Nbr& n, const C (*__restrict__ uw)[3], C f[])
+{
+    if constexpr (WALLS) {
+        sfor<0, L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int d = L::opp(i);
+            const int face = out_face<L, d>(n);
+            if (face >= 0) {
+                const C cuw = (C)L::c(d, 0) * uw[face][0] + (C)L::c(d, 1) * uw[face][1] +
+                              (C)L::c(d, 2) * uw[face][2];
+                f[i] = f[i] - (C)6 * (C)L::w(d) * cuw;
+            }
+        });
+    }
+}
+
 // Gathers f_i(x) for all i (pull propagation with bounce-back).
 template <class L, typename S, bool WALLS>
 __device__ __forceinline__ void pull(const S* __restrict__ fin, const Geom& g, const Nbr& n, int x,
@@ -456,6 +491,15 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
             }
         }
     }
+    // A moving wall acts on the bounced value after the IS imposition it may have received.
+    if constexpr (WALLS) {
+        if (a.moving_walls && *a.pv.pending) {
+            if constexpr (St::deviation)
+                wall_momentum<L, C, WALLS>(n, a.uw->uf, f);
+            else
+                wall_momentum<L, C, WALLS>(n, a.uw->u, f);
+        }
+    }
 
     float mrho = 0.f, mj0 = 0.f, mj1 = 0.f, mj2 = 0.f;  // pre-collision moments (FP32 path)
     if constexpr (St::deviation)
@@ -604,6 +648,14 @@ __global__ void k_materialize(const MaterializeArgs a)
                                             (const float*)a.stash_in, f);
             else
                 substitute_is_plain<L, WALLS>(g, n, x, y, z, idx, m, a.pv, (const double*)a.stash_in, f);
+        }
+    }
+    if constexpr (WALLS) {
+        if (a.moving_walls && *a.pv.pending) {
+            if constexpr (St::deviation)
+                wall_momentum<L, C, WALLS>(n, a.uw->uf, f);
+            else
+                wall_momentum<L, C, WALLS>(n, a.uw->u, f);
         }
     }
     double fd[Q];

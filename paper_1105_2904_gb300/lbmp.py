@@ -23,7 +23,7 @@ LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16DEV, "bf16": LBM_BF16DEV}
 LBM_PERIODIC, LBM_NOSLIP = 0, 1
 
-EXPORTED = ("lbm_create", "lbm_configure", "lbm_add_particles", "lbm_step", "lbm_synchronize",
+EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
             "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_bs_exchange_noalloc",
             "lbm_last_error", "lbm_destroy")
@@ -52,6 +52,7 @@ def load(path: str = LIB_PATH):
     i32 = ctypes.c_int
     lib.lbm_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, i32, ctypes.c_double, D]
     lib.lbm_configure.argtypes = [P, i32, I, D, ctypes.c_double, i32, P]
+    lib.lbm_set_wall_velocity.argtypes = [P, i32, D]
     lib.lbm_add_particles.argtypes = [P, i32, D, D, D, D, D, I]
     lib.lbm_step.argtypes = [P, i32]
     lib.lbm_synchronize.argtypes = [P]
@@ -112,6 +113,11 @@ def lbm_configure(h, precision, faces=None, particle_gravity=None, contact_gap=0
                                 None if fa is None else fa.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                 _dp(g), float(contact_gap), int(bool(body_force_on_particles)),
                                 ctypes.c_void_p(cuda_stream) if cuda_stream else None))
+
+
+def lbm_set_wall_velocity(h, face, u):
+    u = _f64(u, 3)
+    _check(h, load().lbm_set_wall_velocity(h, int(face), _dp(u)))
 
 
 def lbm_add_particles(h, centers, radii, densities, velocities=None, omegas=None):
@@ -210,7 +216,7 @@ class Simulation:
 
     def __init__(self, lattice, nx, ny, nz, tau, body_force=(0.0, 0.0, 0.0), precision="fp32",
                  walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False,
-                 cuda_stream=None):
+                 cuda_stream=None, wall_velocity=None):
         self.lattice = lattice
         self.Q = 9 if lattice == LBM_D2Q9 else 19
         self.shape = (nz, ny, nx)
@@ -220,6 +226,8 @@ class Simulation:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         try:
             lbm_configure(self.h, prec, faces, gravity, gap, body_force_on_particles, cuda_stream)
+            for face, u in (wall_velocity or {}).items():
+                lbm_set_wall_velocity(self.h, face, u)
         except Exception:
             lbm_destroy(self.h)
             self.h = None
@@ -233,6 +241,9 @@ class Simulation:
 
     def __del__(self):
         self.close()
+
+    def set_wall_velocity(self, face, u):
+        lbm_set_wall_velocity(self.h, face, u)
 
     def add_particles(self, centers, radii, densities, velocities=None, omegas=None):
         first = lbm_add_particles(self.h, centers, radii, densities, velocities, omegas)

@@ -195,3 +195,26 @@ def test_uniform_flow_is_a_fixed_point(lattice, shape):
     s.set_f(f)
     s.step(10)
     assert np.max(np.abs(s.get_f() - f)) < 1e-15
+
+
+@pytest.mark.parametrize("lattice", [O.D2Q9, O.D3Q19])
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.3])
+def test_couette_profile_is_exact(lattice, tau):
+    # Walls at y = -1/2 and ny - 1/2 moving at -U and +U (velocity-imposed boundaries of
+    # Secs. 3.1-3.2): the steady profile is exactly linear at any tau.
+    ny, U = 16, 0.02
+    s = O.OracleSim(lattice, 1, ny, 1, tau, walls=(0, 1, 0), wall_velocity={2: (-U, 0, 0), 3: (U, 0, 0)})
+    s.step(20000)
+    rho, u = s.get_fields()
+    y = np.arange(ny)
+    exact = -U + 2.0 * U * (y + 0.5) / ny
+    assert np.max(np.abs(u[0, :, 0, 0] - exact)) / U < 1e-10
+    assert np.max(np.abs(u[0, :, 0, 1:])) < 1e-13
+    assert np.max(np.abs(rho - 1.0)) < 1e-10
+
+
+def test_wall_velocity_must_be_tangential_and_on_a_wall():
+    with pytest.raises(ValueError):
+        O.OracleSim(O.D2Q9, 8, 8, 1, 0.8, walls=(0, 1, 0), wall_velocity={3: (0.0, 0.01, 0.0)})
+    with pytest.raises(ValueError):
+        O.OracleSim(O.D2Q9, 8, 8, 1, 0.8, walls=(0, 1, 0), wall_velocity={0: (0.0, 0.01, 0.0)})
