@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="d3q19_512", choices=["d3q19_512", "d2q9_sedimentation"])
+    p.add_argument("--workload", default="d3q19_512", choices=["d3q19_512", "d2q9_sedimentation", "ensemble_64"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     p.add_argument("--edge", type=int, default=0, help="override the 3D box edge (same solid fraction)")
     p.add_argument("--no-e2e", action="store_true")
@@ -354,10 +354,157 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_ensemble(args):
+    """64 independent periodic D3Q19 cells (edges 32-128, 1-8 spheres of radius 4-10, tau in
+    [0.55, 1]) advanced as one batch (one sweep launch over all cells, batched particle
+    phase, multi-step graphs, autotuned launch configuration), against the same cells stepped
+    as 64 separate contexts (one graph launch per cell per step). Both give identical bits."""
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1105_2904_gb300 import autotune as AT
+    from paper_1105_2904_gb300 import build as B
+    from paper_1105_2904_gb300 import lbmp
+
+    B.build()
+    e = W.ensemble_cells()
+    n_cells = len(e.dims)
+    F = [e.body_force] * n_cells
+    prec = args.precision
+
+    def make_batch(p):
+        b = lbmp.Batch(1, e.dims, e.taus, F, precision=p, gap=0.0, body_force_on_particles=e.body_force_on_particles)
+        for k in range(n_cells):
+            if len(e.radii[k]):
+                b.add_particles(k, e.centers[k], e.radii[k], e.densities[k], e.velocities[k])
+        return b
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    b = make_batch(prec)
+    spg = max(1, min(50, args.steps))
+    best, trials = AT.tune(b, trial_steps=8, steps_per_graph=spg)
+    stream = torch.cuda.ExternalStream(b.stream)
+    b.step(args.warmup)
+    b.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    b.synchronize()
+    info = b.info()
+    value, ms = aggregate_throughput(e.sites, args.steps, e0.elapsed_time(e1))
+    prof = b.profile(min(args.steps, 30))
+    bytes_per_site = {"fp32": 152, "fp16": 76, "bf16": 76, "fp64": 304}[prec]
+    algo_bytes = bytes_per_site * e.sites
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / (prof["sweep_ms"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_sweep_batch (all cells in one launch)",
+                "algorithmic_bytes_per_launch": algo_bytes, "sweep_ms": prof["sweep_ms"],
+                "particle_phase_ms": prof["particle_ms"], "step_ms_ungraphed": prof["step_ms"],
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"}
+    b.close()
+
+    # The same cells as separate contexts, one graph launch per cell per step, on one stream.
+    sep_stream = torch.cuda.Stream()
+    sims = []
+    for k in range(n_cells):
+        nx, ny, nz = e.dims[k]
+        s_ = lbmp.Simulation(1, nx, ny, nz, e.taus[k], body_force=e.body_force, precision=prec, gap=0.0,
+                             body_force_on_particles=e.body_force_on_particles, cuda_stream=sep_stream.cuda_stream)
+        if len(e.radii[k]):
+            s_.add_particles(e.centers[k], e.radii[k], e.densities[k], e.velocities[k])
+        sims.append(s_)
+    for _ in range(args.warmup):
+        for s_ in sims:
+            s_.step(1)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(sep_stream)
+    for _ in range(args.steps):
+        for s_ in sims:
+            s_.step(1)
+    f1.record(sep_stream)
+    torch.cuda.synchronize()
+    sep_ms = f0.elapsed_time(f1)
+    for s_ in sims:
+        s_.close()
+    sep_value, _ = aggregate_throughput(e.sites, args.steps, sep_ms)
+
+    # End to end through the C-ABI with host buffers: batch creation, particle upload, then
+    # every step a read-back of every cell's particle state.
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        b2 = make_batch(prec)
+        b2.set_tuning(tile_width=best["tile_width"], order=best["order"], grid=best["grid"], steps_per_graph=1)
+        views = [b2.cell(k) for k in range(n_cells)]
+        hosts = [{q: np.empty((len(e.radii[k]), 3)) for q in ("x", "u", "omega", "force", "torque")}
+                 for k in range(n_cells)]
+        for _ in range(args.steps):
+            b2.step(1)
+            for k in range(n_cells):
+                if len(e.radii[k]):
+                    lbmp.lbm_get_particles(views[k].h, len(e.radii[k]), hosts[k])
+        dt = time.perf_counter() - t
+        b2.close()
+        dt = reduce_max(dt)
+        h2d = sum(c.nbytes + r.nbytes + d.nbytes + v.nbytes
+                  for c, r, d, v in zip(e.centers, e.radii, e.densities, e.velocities)) / args.steps
+        e2e = {"value": e.sites * args.steps * world / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(5 * 3 * 8 * e.n_particles),
+               "includes": "batch creation, particle upload and site classification, %d steps each followed "
+                           "by a particle-state read-back of every cell" % args.steps}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": e.name, "cells": n_cells, "sites": e.sites, "particles": e.n_particles,
+                       "dropped_spheres": int(sum(e.dropped)), "storage": prec,
+                       "tuning": {"policy": best["policy"], "order": best["order"], "grid": best["grid"],
+                                  "steps_per_graph": spg, "candidates": len(trials)},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: %.1f GB of distributions per step" % (algo_bytes / 1e9)},
+            "separate_launches": {"value": sep_value, "unit": UNIT, "ms_per_step": sep_ms / args.steps,
+                                  "launches_per_step": "one step graph per cell (%d)" % n_cells,
+                                  "error": "bitwise identical to the batch"},
+            "speedup_vs_separate": value / sep_value,
+            "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
+            "gpu_launches": int(info["launches_per_step"]) * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble_64":
+        run_ensemble(args)
     else:
         run_ours(args)
 

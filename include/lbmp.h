@@ -39,7 +39,8 @@
 extern "C" {
 #endif
 
-typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+typedef struct lbm_ctx lbm_ctx;     /* opaque, library-owned */
+typedef struct lbm_batch lbm_batch; /* opaque, library-owned: an ensemble of contexts */
 
 typedef enum {
     LBM_OK = 0,
@@ -209,6 +210,74 @@ lbm_status lbm_bs_exchange_noalloc(int lattice, int nx, int ny, int nz, const in
                                    const unsigned* tags, int n, const double* centers,
                                    const double* velocities, const double* omegas,
                                    double* force, double* torque, void* cuda_stream);
+
+/* ---- Batched ensembles ------------------------------------------------------------------
+ * Many independent simulations ("cells", e.g. periodic boxes of different sizes, each with
+ * its own tau, body force and particles) advanced together. The paper simulates one box at
+ * a time; the batch only changes how the work is launched: every step runs one sweep
+ * launch over all cells (a schedule table of 128-thread tiles, each tile one rectangle of
+ * one x-y plane of one cell) and one launch per particle-phase kernel (the cell as the
+ * second grid index), captured in CUDA graphs of one or several steps. Each cell's result
+ * is bit for bit the result of stepping it alone. */
+
+/* Creates ncells contexts sharing the lattice, storage precision, face kinds, particle
+ * gravity, contact gap and force-on-particles flag (meaning as lbm_configure); dims
+ * (ncells*3: nx, ny, nz), tau (ncells) and body_force (ncells*3, may be NULL = 0) are per
+ * cell. All cells enqueue on one library-created stream (lbm_batch_stream).
+ * Errors as lbm_create / lbm_configure; *out is NULL on error. */
+lbm_status lbm_batch_create(lbm_batch** out, int lattice, int ncells, const int* dims, const double* tau,
+                            const double* body_force, int precision, const int faces[6],
+                            const double particle_gravity[3], double contact_gap,
+                            int body_force_on_particles);
+
+/* lbm_add_particles on cell `cell` (before the first step). Errors as lbm_add_particles,
+ * LBM_E_INVALID for a cell index out of range. */
+lbm_status lbm_batch_add_particles(lbm_batch* b, int cell, int n, const double* centers, const double* radii,
+                                   const double* densities, const double* velocities, const double* omegas);
+
+/* The context of one cell (owned by the batch; NULL if out of range). Every single-context
+ * getter and setter works on it (lbm_get_fields, lbm_get_particles, lbm_set_distributions,
+ * lbm_set_wall_velocity, ...); lbm_step on it advances that cell alone with its own graph.
+ * Cells must share their buffer parity when the batch steps (an odd number of single-cell
+ * steps on one cell makes lbm_batch_step return LBM_E_STATE). */
+lbm_ctx* lbm_batch_cell(lbm_batch* b, int cell);
+
+/* Launch tuning (results do not depend on it):
+ *   tile_width[ncells]: sites along x of a cell's tiles, 32, 64 or 128 (the tile then spans
+ *     128/width rows in y); NULL = 128 for every cell;
+ *   order: 0 cells one after another, 1 one tile of each cell in turn, 2 largest cell first;
+ *   grid: 0 = one block per tile, > 0 = that many resident blocks striding over the table;
+ *   steps_per_graph: steps captured in one graph launch (1..256).
+ * Re-captures the step graphs at the next step. LBM_E_INVALID on a bad value. */
+lbm_status lbm_batch_set_tuning(lbm_batch* b, const int* tile_width, int order, int grid, int steps_per_graph);
+
+/* Advances every cell by n steps (asynchronous, like lbm_step). */
+lbm_status lbm_batch_step(lbm_batch* b, int n);
+
+/* Waits for the batch's stream; returns the first non-OK device status of any cell. */
+lbm_status lbm_batch_synchronize(lbm_batch* b);
+
+/* As lbm_profile_steps, for the whole batch: out_ms = mean sweep, particle phase, step. */
+lbm_status lbm_batch_profile_steps(lbm_batch* b, int n, double out_ms[3]);
+
+/* out[0] cells, out[1] lattice sites of all cells, out[2] particles, out[3] sweep tiles,
+ * out[4] kernels launched per step. Captures the step graphs if needed. */
+lbm_status lbm_batch_get_info(lbm_batch* b, long long out[5]);
+
+/* The cudaStream_t every cell of the batch enqueues on. */
+void* lbm_batch_stream(lbm_batch* b);
+
+/* Host-only (no device needed): the sweep schedule of a batch. Returns the number of tiles
+ * for ncells cells of sizes dims[ncells*3] with tile_width[ncells] (NULL = 128) in the given
+ * order (as lbm_batch_set_tuning), or -1 on a bad argument. If out != NULL it receives 4
+ * ints per tile in launch order: cell, x0, y0 | (log2(width) << 16), z. */
+long long lbm_schedule_tiles(int ncells, const int* dims, const int* tile_width, int order, int* out);
+
+/* Description of the last non-OK status of b (never NULL). */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Destroys the batch and all of its cells (NULL is a no-op). */
+void lbm_batch_destroy(lbm_batch* b);
 
 /* Description of the last non-OK status of ctx (static storage; never NULL). */
 const char* lbm_last_error(const lbm_ctx* ctx);

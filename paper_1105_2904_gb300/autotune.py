@@ -1,0 +1,124 @@
+"""Launch tuner for batched ensembles.
+
+The batch's results do not depend on its launch configuration (every tuning gives the same
+bits), only its speed does. The tuner times candidate configurations on the batch itself,
+through ``lbm_batch_profile_steps`` (CUDA events around the sweep launch), and keeps the
+fastest:
+
+- tile width per cell: 32, 64 or 128 sites along x per 128-thread tile, uniform or chosen per
+  cell to minimise the padded (idle) threads of ragged cell edges;
+- schedule order: cells one after another, round robin, or largest first;
+- grid: one block per tile, or a persistent grid of resident blocks striding over the table.
+
+Storage precision is the third axis: ``choose_precision`` keeps the precisions whose
+measured error against the FP64 oracle meets the caller's tolerance, times each, and returns
+the fastest. Results are cached in a JSON file keyed by the shape class of the batch.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+WIDTHS = (32, 64, 128)
+
+# Velocity error against the FP64 oracle, relative to max|u|, measured by the parity tests
+# (200-300 steps of a suspension): FP64 exact, FP32 deviations 1e-5, FP16 / BF16 scaled
+# deviations 2.4e-4 / 1.8e-3.
+ERROR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 2.4e-4, "bf16": 1.8e-3}
+
+
+def padded_sites(nx, ny, w):
+    """Threads a plane of nx x ny sites occupies with tiles w wide and 128 / w rows high."""
+    h = 128 // w
+    return -(-nx // w) * w * (-(-ny // h) * h)
+
+
+def min_waste_width(nx, ny):
+    """Tile width with the fewest idle threads per plane (ties: the wider tile)."""
+    return min(WIDTHS, key=lambda w: (padded_sites(nx, ny, w), -w))
+
+
+def width_policies(dims):
+    out = {"min_waste": [min_waste_width(nx, ny) for nx, ny, _ in dims]}
+    for w in WIDTHS:
+        out[str(w)] = [w] * len(dims)
+    return out
+
+
+def candidates(dims, sms=152, resident=8):
+    """Candidate tunings (dicts for Batch.set_tuning, plus a 'policy' label)."""
+    for name, widths in width_policies(dims).items():
+        for order in (0, 1, 2):
+            for grid in (0, sms * resident):
+                yield {"policy": name, "tile_width": widths, "order": order, "grid": grid}
+
+
+def shape_key(lattice, precision, dims, particles):
+    """Shape class: lattice, precision, the sorted cell sizes rounded up to 16 and the
+    particle count rounded to a power of two."""
+    r16 = sorted(tuple(-(-v // 16) * 16 for v in d) for d in dims)
+    p2 = 1
+    while p2 < max(1, particles):
+        p2 *= 2
+    return "%s|%s|%s|%d" % (lattice, precision, ";".join("x".join(map(str, d)) for d in r16), p2)
+
+
+def _load(cache):
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            return json.load(f)
+    return {}
+
+
+def _store(cache, table):
+    if not cache:
+        return
+    tmp = cache + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, cache)
+
+
+def tune(batch, trial_steps=8, steps_per_graph=10, cache=None, key=None, timer=None, cands=None):
+    """Times every candidate on `batch` and leaves the fastest set. `timer(batch, n)` returns
+    the sweep time in ms (default: lbm_batch_profile_steps); the trial steps advance the
+    batch. Returns (best, results) with results = [(sweep_ms, candidate)] in trial order."""
+    table = _load(cache)
+    if key and key in table:
+        best = table[key]
+        batch.set_tuning(tile_width=best["tile_width"], order=best["order"], grid=best["grid"],
+                         steps_per_graph=steps_per_graph)
+        return best, []
+    timer = timer or (lambda b, n: b.profile(n)["sweep_ms"])
+    results = []
+    for c in (cands if cands is not None else candidates(batch.dims)):
+        batch.set_tuning(tile_width=c["tile_width"], order=c["order"], grid=c["grid"], steps_per_graph=1)
+        timer(batch, 2)  # re-capture and warm up
+        results.append((float(timer(batch, trial_steps)), c))
+    best = min(results, key=lambda t: t[0])[1]
+    batch.set_tuning(tile_width=best["tile_width"], order=best["order"], grid=best["grid"],
+                     steps_per_graph=steps_per_graph)
+    if key:
+        table[key] = dict(best)
+        _store(cache, table)
+    return best, results
+
+
+def choose_precision(make_batch, max_error, precisions=("fp32", "fp16", "bf16"), trial_steps=8, timer=None):
+    """Among the precisions whose error bound meets `max_error`, the one whose tuned sweep is
+    fastest. `make_batch(precision)` builds a fresh batch. Returns (precision, {precision:
+    (sweep_ms, tuning)})."""
+    timer = timer or (lambda b, n: b.profile(n)["sweep_ms"])
+    out = {}
+    for p in precisions:
+        if ERROR_BOUND[p] > max_error:
+            continue
+        b = make_batch(p)
+        try:
+            best, res = tune(b, trial_steps=trial_steps, timer=timer)
+            out[p] = (min(r[0] for r in res), best)
+        finally:
+            b.close()
+    if not out:
+        raise ValueError("no storage precision meets the error tolerance %g" % max_error)
+    return min(out, key=lambda p: out[p][0]), out

@@ -10,115 +10,13 @@
 #include <thread>
 #include <vector>
 
-#include "kernels.h"
-#include "lbmp.h"
+#include "ctx.h"
 
 using namespace lbmp;
+using namespace lbmp::host;
 
-namespace {
-constexpr double LBM_PI = 3.14159265358979323846;
-constexpr int PAIR_CAP = 16384;
-constexpr size_t STAGING_BYTES = 64ull << 20;
-}  // namespace
-
-struct lbm_ctx {
-    int lattice = 1, Q = 19, D = 3;
-    Geom g{};
-    double tau = 0.6, F[3] = {0, 0, 0};
-    int precision = LBM_FP32;
-    const KernelTable* kt = nullptr;
-    double grav[3] = {0, 0, 0};
-    double uw[6][3] = {};      // tangential velocity of each wall face (host copy)
-    bool moving_walls = false; // set once a face is given a velocity; never cleared
-    WallVel* wv = nullptr;     // device: [0] velocities of the pending streaming, [1] current
-    double gap = 0.0;
-    int bfp = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    bool allocated = false;
-    bool stepped = false;
-
-    void* f[2] = {nullptr, nullptr};
-    void* stash[2] = {nullptr, nullptr};
-    unsigned* tag = nullptr;
-    unsigned* ismask = nullptr;
-    void* bs_scratch = nullptr;
-    int cur = 0;
-
-    int np = 0;
-    std::vector<PConst> h_pc;
-    std::vector<PKern> h_pk;
-    std::vector<PKernF> h_pkf;
-    std::vector<double> h_x;
-    std::vector<int> h_tmpl;
-    PKern* pk = nullptr;
-    PKernF* pkf = nullptr;
-    PConst* pc = nullptr;
-    int* tmpl = nullptr;
-    double *x = nullptr, *un = nullptr, *acc = nullptr, *force = nullptr;
-    int* Kold = nullptr;
-    Counters* cnt = nullptr;
-    int* status = nullptr;
-    int* pending = nullptr;
-    unsigned* step_id = nullptr;
-    CellGrid cg{};
-    int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_cursor = nullptr,
-        *cell_items = nullptr;
-    unsigned long long* pairs = nullptr;
-    int *changed = nullptr, *restamp = nullptr, *restamp_flag = nullptr;
-
-    double* staging = nullptr;
-    void* pinned = nullptr;  // page-locked host staging for particle read-backs
-    size_t pinned_bytes = 0;
-    double* pout = nullptr;  // [15][np] packed particle state on the device
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int launches_per_step = 0;
-    long long steps = 0;
-    size_t dev_bytes = 0;
-    std::vector<void*> allocs;
-    std::string err;
-};
-
-namespace {
-
-lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg)
-{
-    if (c) c->err = msg;
-    return s;
-}
-
-lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what)
-{
-    return fail(c, LBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-#define CK(call)                                                       \
-    do {                                                               \
-        cudaError_t e_ = (call);                                       \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
-    } while (0)
-
-template <typename T>
-lbm_status dev_alloc(lbm_ctx* ctx, T** p, size_t bytes)
-{
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, LBM_E_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " +
-                                        cudaGetErrorString(e));
-    }
-    ctx->allocs.push_back(q);
-    ctx->dev_bytes += bytes;
-    *p = (T*)q;
-    return LBM_OK;
-}
-
-#define CS(call)                                 \
-    do {                                         \
-        lbm_status s_ = (call);                  \
-        if (s_ != LBM_OK) return s_;             \
-    } while (0)
+namespace lbmp {
+namespace host {
 
 const KernelTable* table_for(int precision)
 {
@@ -301,16 +199,8 @@ PartView part_view(lbm_ctx* ctx)
     return v;
 }
 
-template <class A>
-void wall_args(const lbm_ctx* ctx, A& a)
-{
-    a.moving_walls = ctx->moving_walls ? 1 : 0;
-    a.uw = ctx->wv;
-}
-
-// One time step on ctx->stream, reading buffer c and writing buffer 1 - c. With ev != nullptr
-// CUDA events are recorded before the sweep, after it, and after the particle phase.
-int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
+// Arguments of the sweep that reads buffer c and writes buffer 1 - c.
+SweepArgs sweep_args(lbm_ctx* ctx, int c)
 {
     SweepArgs a{};
     a.lattice = ctx->lattice;
@@ -328,23 +218,37 @@ int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
     a.pre_f = (float)a.pre;
     for (int k = 0; k < 3; ++k) a.F_f[k] = (float)ctx->F[k];
     wall_args(ctx, a);
+    return a;
+}
+
+// Arguments of the IS-density fix-up after a step that wrote buffer 1 - c.
+StashFixArgs stash_fix_args(lbm_ctx* ctx, int c)
+{
+    StashFixArgs s{};
+    s.lattice = ctx->lattice;
+    s.g = ctx->g;
+    s.fout = ctx->f[1 - c];
+    s.stash_out = ctx->stash[1 - c];
+    s.pk = ctx->pk;
+    s.pc = ctx->pc;
+    s.tmpl = ctx->tmpl;
+    s.list = ctx->changed;
+    s.cnt = ctx->cnt;
+    return s;
+}
+
+// One time step on ctx->stream, reading buffer c and writing buffer 1 - c. With ev != nullptr
+// CUDA events are recorded before the sweep, after it, and after the particle phase.
+int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
+{
+    const SweepArgs a = sweep_args(ctx, c);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
     ctx->kt->sweep(a, ctx->stream);
     if (ev) cudaEventRecord(ev[1], ctx->stream);
     int launches = 1;
     if (ctx->np > 0) {
         launches += launch_particle_phase(particle_args(ctx), ctx->stream);
-        StashFixArgs s{};
-        s.lattice = ctx->lattice;
-        s.g = ctx->g;
-        s.fout = ctx->f[1 - c];
-        s.stash_out = ctx->stash[1 - c];
-        s.pk = ctx->pk;
-        s.pc = ctx->pc;
-        s.tmpl = ctx->tmpl;
-        s.list = ctx->changed;
-        s.cnt = ctx->cnt;
-        ctx->kt->stash_fix(s, ctx->stream);
+        ctx->kt->stash_fix(stash_fix_args(ctx, c), ctx->stream);
         ctx->kt->update_masks(mask_args(ctx, true), ctx->stream);
         launches += 2;
     }
@@ -388,7 +292,8 @@ lbm_status sync_status(lbm_ctx* ctx)
     return LBM_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace lbmp
 
 extern "C" {
 

@@ -1,0 +1,140 @@
+// Host-side state of a simulation context and the helpers shared by the single-context
+// entry points (api.cu) and the batched ensemble (batch.cu). Internal: not installed.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "lbmp.h"
+
+namespace lbmp {
+namespace host {
+constexpr double LBM_PI = 3.14159265358979323846;
+constexpr int PAIR_CAP = 16384;
+constexpr size_t STAGING_BYTES = 64ull << 20;
+}  // namespace host
+}  // namespace lbmp
+
+// One simulation: the lattice, its storage and particles, and the captured step graphs.
+struct lbm_ctx {
+    int lattice = 1, Q = 19, D = 3;
+    lbmp::Geom g{};
+    double tau = 0.6, F[3] = {0, 0, 0};
+    int precision = LBM_FP32;
+    const lbmp::KernelTable* kt = nullptr;
+    double grav[3] = {0, 0, 0};
+    double uw[6][3] = {};      // tangential velocity of each wall face (host copy)
+    bool moving_walls = false; // set once a face is given a velocity; never cleared
+    lbmp::WallVel* wv = nullptr;     // device: [0] velocities of the pending streaming, [1] current
+    double gap = 0.0;
+    int bfp = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool allocated = false;
+    bool stepped = false;
+
+    void* f[2] = {nullptr, nullptr};
+    void* stash[2] = {nullptr, nullptr};
+    unsigned* tag = nullptr;
+    unsigned* ismask = nullptr;
+    void* bs_scratch = nullptr;
+    int cur = 0;
+
+    int np = 0;
+    std::vector<lbmp::PConst> h_pc;
+    std::vector<lbmp::PKern> h_pk;
+    std::vector<lbmp::PKernF> h_pkf;
+    std::vector<double> h_x;
+    std::vector<int> h_tmpl;
+    lbmp::PKern* pk = nullptr;
+    lbmp::PKernF* pkf = nullptr;
+    lbmp::PConst* pc = nullptr;
+    int* tmpl = nullptr;
+    double *x = nullptr, *un = nullptr, *acc = nullptr, *force = nullptr;
+    int* Kold = nullptr;
+    lbmp::Counters* cnt = nullptr;
+    int* status = nullptr;
+    int* pending = nullptr;
+    unsigned* step_id = nullptr;
+    lbmp::CellGrid cg{};
+    int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_cursor = nullptr,
+        *cell_items = nullptr;
+    unsigned long long* pairs = nullptr;
+    int *changed = nullptr, *restamp = nullptr, *restamp_flag = nullptr;
+
+    double* staging = nullptr;
+    void* pinned = nullptr;  // page-locked host staging for particle read-backs
+    size_t pinned_bytes = 0;
+    double* pout = nullptr;  // [15][np] packed particle state on the device
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int launches_per_step = 0;
+    long long steps = 0;
+    size_t dev_bytes = 0;
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+namespace lbmp {
+namespace host {
+
+inline lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+inline lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, LBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                       \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
+    } while (0)
+
+template <typename T>
+lbm_status dev_alloc(lbm_ctx* ctx, T** p, size_t bytes)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LBM_E_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " +
+                                        cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    ctx->dev_bytes += bytes;
+    *p = (T*)q;
+    return LBM_OK;
+}
+
+#define CS(call)                                 \
+    do {                                         \
+        lbm_status s_ = (call);                  \
+        if (s_ != LBM_OK) return s_;             \
+    } while (0)
+
+template <class A>
+void wall_args(const lbm_ctx* ctx, A& a)
+{
+    a.moving_walls = ctx->moving_walls ? 1 : 0;
+    a.uw = ctx->wv;
+}
+
+const KernelTable* table_for(int precision);
+lbm_status ensure_alloc(lbm_ctx* ctx);
+lbm_status sync_status(lbm_ctx* ctx);
+ParticleArgs particle_args(lbm_ctx* ctx);
+MaskArgs mask_args(lbm_ctx* ctx, bool restamp_list);
+PartView part_view(lbm_ctx* ctx);
+SweepArgs sweep_args(lbm_ctx* ctx, int c);
+StashFixArgs stash_fix_args(lbm_ctx* ctx, int c);
+
+}  // namespace host
+}  // namespace lbmp

@@ -82,6 +82,19 @@ struct MaskArgs {
     int np;
 };
 
+// One sweep launch over a batch of independent cells. Entry e of the schedule table is one
+// 128-thread tile of one cell: (cell, x0, y0 | log2(tile width) << 16, z); the tile covers
+// x0 .. x0 + w - 1 and y0 .. y0 + 128/w - 1 of plane z (w = 32, 64 or 128).
+struct BatchSweepArgs {
+    int lattice;
+    const SweepArgs* cells;    // device [ncells], this step's buffer parity
+    const int4* table;         // device [ntiles]
+    int ntiles;
+    int walls;                 // some cell has walls
+    int part;                  // some cell has particles
+    int grid;                  // 0: one block per tile; > 0: that many blocks stride over the table
+};
+
 struct KernelTable {
     void (*sweep)(const SweepArgs&, cudaStream_t);
     void (*update_masks)(const MaskArgs&, cudaStream_t);
@@ -90,6 +103,10 @@ struct KernelTable {
     void (*unstream)(const UnstreamArgs&, cudaStream_t);
     void (*fill_rest)(int lattice, void* dst, unsigned N, cudaStream_t);
     void (*stash_fix)(const StashFixArgs&, cudaStream_t);
+    void (*sweep_batch)(const BatchSweepArgs&, cudaStream_t);
+    // per-cell argument arrays on the device, blockIdx.y = cell
+    void (*stash_fix_batch)(int lattice, const StashFixArgs* cells, int ncells, cudaStream_t);
+    void (*update_masks_batch)(int lattice, const MaskArgs* cells, int ncells, cudaStream_t);
     int elem_bytes;
     int compute_bytes;
 };
@@ -145,6 +162,17 @@ struct ParticleArgs {
 int launch_particle_phase(const ParticleArgs& a, cudaStream_t s);
 // Stamps every particle's site set into a cleared owner map (after lbm_add_particles).
 void launch_stamp_all(const ParticleArgs& a, cudaStream_t s);
+
+// Shape of a batched particle phase: the largest per-cell counts size the grids
+// (blockIdx.y = cell; blocks beyond a cell's own counts return at once).
+struct PhaseShape {
+    int ncells;
+    int max_np;       // particles of the most populated cell
+    int max_cells;    // contact-grid cells of the largest cell
+    int pair_cap;     // contact-pair capacity of every cell (its resolve buffer)
+    int scratch_f64;  // FP64 storage: ordered per-particle sums
+};
+int launch_particle_phase_batch(const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s);
 // After a sweep with moving walls: the current wall velocities become those of the streaming
 // that the next pull completes (wv[0] <- wv[1]), and the pulled values await streaming.
 void launch_wall_advance(WallVel* wv, int* pending, cudaStream_t s);

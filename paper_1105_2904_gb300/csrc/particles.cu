@@ -5,6 +5,8 @@
 //   trigger, pairs processed in (i, j) order), position update (Eq. 13) and the integer
 //   shift of each site set (Eqs. 14-15), then the incremental re-marking of the owner map
 //   for the particles whose shift changed and their neighbours.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace lbmp {
@@ -14,6 +16,34 @@ namespace {
 constexpr int PT = 128;  // threads per block of the per-particle kernels
 
 __device__ inline void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// Arguments of the simulation a block works on: the kernel parameter for a single context,
+// entry blockIdx.y of a device array for a batch of cells (each entry's pointers address
+// that cell's own arrays, so particle and site indices stay local to the cell).
+template <bool B>
+__device__ __forceinline__ ParticleArgs cell_args(const ParticleArgs& a0, const ParticleArgs* __restrict__ cells)
+{
+    if constexpr (B)
+        return cells[blockIdx.y];
+    else
+        return a0;
+}
+
+// Per-step clearing of the work-list counters, the contact cell counts and cursors, and the
+// re-stamp flags.
+template <bool B>
+__global__ void k_phase_clear(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
+{
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, T = gridDim.x * blockDim.x;
+    if (t0 == 0) *a.cnt = Counters{0, 0, 0, 0};
+    for (int i = t0; i < a.cg.total; i += T) {
+        a.cell_count[i] = 0;
+        a.cell_cursor[i] = 0;
+    }
+    for (int i = t0; i < a.np; i += T) a.restamp_flag[i] = 0;
+}
 
 // d - n floor(d/n + 1/2). For |d| < n/4, d/n + 1/2 lies in (1/4, 3/4) whatever the
 // rounding, so the floor is 0 and the result is d itself: skip the FP64 division.
@@ -32,8 +62,11 @@ __device__ inline bool periodic_axis(const Geom& g, int k, int D) { return k < D
 // Fixed-order sums of the per-site momentum exchange of each particle (Eqs. 8-9) over the
 // sites it owns as BS, in template order (z, y, x lexicographic offsets). FP64 mode: one
 // thread per particle, strictly sequential, the order a direct implementation uses.
-__global__ void k_reduce_ordered(const ParticleArgs a)
+template <bool B>
+__global__ void k_reduce_ordered(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
     const PConst pc = a.pc[p];
@@ -59,10 +92,14 @@ __global__ void k_reduce_ordered(const ParticleArgs a)
 // owned it as BS in the sweep and the step it was written in, so no owner-map read is
 // needed.
 constexpr int RT = 128;
-__global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a)
+template <bool B>
+__global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     __shared__ float part[RT / 32][6];
     const int p = blockIdx.x;
+    if (p >= a.np) return;
     const PConst pc = a.pc[p];
     const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
     const unsigned code = (CLS_BS << 30) | (unsigned)p;
@@ -133,8 +170,11 @@ __device__ inline int cell_coord(const ParticleArgs& a, int k, double x)
 }
 
 // Eqs. 10-11 (+ external increment), force/torque output, cell of the current centre.
-__global__ void k_accel(const ParticleArgs a)
+template <bool B>
+__global__ void k_accel(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
     const PConst pc = a.pc[p];
@@ -160,8 +200,11 @@ __global__ void k_accel(const ParticleArgs a)
 }
 
 // Exclusive scan of the cell counts (one block).
-__global__ void k_cell_scan(const ParticleArgs a)
+template <bool B>
+__global__ void k_cell_scan(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     __shared__ int part[1024];
     const int n = a.cg.total;
     const int T = blockDim.x;
@@ -186,8 +229,11 @@ __global__ void k_cell_scan(const ParticleArgs a)
     if (threadIdx.x == T - 1) a.cell_start[n] = part[T - 1];
 }
 
-__global__ void k_cell_fill(const ParticleArgs a)
+template <bool B>
+__global__ void k_cell_fill(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
     const int c = a.cell_of[p];
@@ -214,8 +260,11 @@ __device__ inline int nbr_cells(const ParticleArgs& a, int k, int c, int out[3])
 
 // Candidate pairs (i < j) whose predicted centres overlap: |(x_i+u_i')-(x_j+u_j')| < r_i+r_j+gap.
 // One thread per (particle, neighbouring cell): up to 27 threads per particle.
-__global__ void k_pairs(const ParticleArgs a)
+template <bool B>
+__global__ void k_pairs(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / 27, cn = t % 27;
     if (i >= a.np) return;
@@ -257,8 +306,11 @@ __global__ void k_pairs(const ParticleArgs a)
 }
 
 // One block: sort the candidate pairs and resolve them serially in (i, j) order.
-__global__ void k_resolve(const ParticleArgs a)
+template <bool B>
+__global__ void k_resolve(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     extern __shared__ unsigned long long keys[];
     const int D = a.lattice == 0 ? 2 : 3;
     const int T = blockDim.x;
@@ -314,8 +366,11 @@ __global__ void k_resolve(const ParticleArgs a)
 
 // Walls, position update (Eq. 13), new shifts (Eqs. 14-15) and the list of particles whose
 // shift changed; one thread per particle.
-__global__ void k_move(const ParticleArgs a)
+template <bool B>
+__global__ void k_move(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     const int D = a.lattice == 0 ? 2 : 3;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p == 0) {
@@ -370,8 +425,11 @@ __device__ inline void add_restamp(const ParticleArgs& a, int q)
 }
 
 // Particles whose site sets may meet the old or new set of a moved particle.
-__global__ void k_mark_neighbours(const ParticleArgs a)
+template <bool B>
+__global__ void k_mark_neighbours(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.cnt->nchanged) return;
     const int D = a.lattice == 0 ? 2 : 3;
@@ -410,8 +468,11 @@ __global__ void k_mark_neighbours(const ParticleArgs a)
 }
 
 // Releases the sites a moved particle owned at its old anchor.
-__global__ void k_mark_clear(const ParticleArgs a)
+template <bool B>
+__global__ void k_mark_clear(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     const int nlist = a.cnt->nchanged;
     for (int b = blockIdx.x; b < nlist; b += gridDim.x) {
         const int p = a.changed[b];
@@ -442,8 +503,11 @@ __device__ inline void stamp_particle(const ParticleArgs& a, int p)
     }
 }
 
-__global__ void k_mark_stamp(const ParticleArgs a)
+template <bool B>
+__global__ void k_mark_stamp(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
+    const ParticleArgs a = cell_args<B>(a0, cells);
+    if (a.np == 0) return;  // a cell of a batch without particles
     const int nlist = a.cnt->nrestamp;
     for (int b = blockIdx.x; b < nlist; b += gridDim.x) stamp_particle(a, a.restamp[b]);
 }
@@ -470,33 +534,48 @@ __global__ void k_pack_particles(const ParticleArgs a, double* out)
     }
 }
 
+template <bool B>
+int particle_phase(const ParticleArgs& a0, const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s)
+{
+    const int nc = sh.ncells;
+    const dim3 gp((sh.max_np + PT - 1) / PT, nc);
+    const int per_cell = std::max(2, mark_grid() / nc);
+    k_phase_clear<B><<<dim3(std::max(1, std::min(64, (std::max(sh.max_np, sh.max_cells) + 255) / 256)), nc), 256, 0, s>>>(
+        a0, cells);
+    if (sh.scratch_f64)
+        k_reduce_ordered<B><<<gp, PT, 0, s>>>(a0, cells);
+    else
+        k_reduce_block<B><<<dim3(sh.max_np, nc), RT, 0, s>>>(a0, cells);
+    k_accel<B><<<gp, PT, 0, s>>>(a0, cells);
+    k_cell_scan<B><<<dim3(1, nc), 1024, 0, s>>>(a0, cells);
+    k_cell_fill<B><<<gp, PT, 0, s>>>(a0, cells);
+    k_pairs<B><<<dim3((sh.max_np * 27 + PT - 1) / PT, nc), PT, 0, s>>>(a0, cells);
+    const size_t smem = sizeof(unsigned long long) * (size_t)sh.pair_cap;
+    const int rthreads = std::min(1024, std::max(32, (sh.pair_cap + 31) / 32 * 32));
+    k_resolve<B><<<dim3(1, nc), rthreads, smem, s>>>(a0, cells);
+    k_move<B><<<gp, PT, 0, s>>>(a0, cells);
+    k_mark_neighbours<B><<<gp, PT, 0, s>>>(a0, cells);
+    k_mark_clear<B><<<dim3(per_cell, nc), 256, 0, s>>>(a0, cells);
+    k_mark_stamp<B><<<dim3(per_cell, nc), 256, 0, s>>>(a0, cells);
+    return 12;
+}
+
 }  // namespace
 
 int launch_particle_phase(const ParticleArgs& a, cudaStream_t s)
 {
-    const int blocks = (a.np + PT - 1) / PT;
-    int launches = 0;
-    cudaMemsetAsync(a.cnt, 0, sizeof(Counters), s);
-    cudaMemsetAsync(a.cell_count, 0, sizeof(int) * (size_t)a.cg.total, s);
-    cudaMemsetAsync(a.cell_cursor, 0, sizeof(int) * (size_t)a.cg.total, s);
-    cudaMemsetAsync(a.restamp_flag, 0, sizeof(int) * (size_t)a.np, s);
-    if (a.scratch_f64)
-        k_reduce_ordered<<<blocks, PT, 0, s>>>(a);
-    else
-        k_reduce_block<<<a.np, RT, 0, s>>>(a);
-    ++launches;
-    k_accel<<<blocks, PT, 0, s>>>(a);
-    k_cell_scan<<<1, 1024, 0, s>>>(a);
-    k_cell_fill<<<blocks, PT, 0, s>>>(a);
-    k_pairs<<<(a.np * 27 + PT - 1) / PT, PT, 0, s>>>(a);
-    const size_t smem = sizeof(unsigned long long) * (size_t)a.pair_cap;
-    k_resolve<<<1, 1024, smem, s>>>(a);
-    k_move<<<blocks, PT, 0, s>>>(a);
-    k_mark_neighbours<<<blocks, PT, 0, s>>>(a);
-    k_mark_clear<<<mark_grid(), 256, 0, s>>>(a);
-    k_mark_stamp<<<mark_grid(), 256, 0, s>>>(a);
-    launches += 9;
-    return launches;
+    PhaseShape sh{};
+    sh.ncells = 1;
+    sh.max_np = a.np;
+    sh.max_cells = a.cg.total;
+    sh.pair_cap = a.pair_cap;
+    sh.scratch_f64 = a.scratch_f64;
+    return particle_phase<false>(a, nullptr, sh, s);
+}
+
+int launch_particle_phase_batch(const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s)
+{
+    return particle_phase<true>(ParticleArgs{}, cells, sh, s);
 }
 
 void launch_pack_particles(const ParticleArgs& a, double* out, cudaStream_t s)
@@ -526,8 +605,10 @@ void launch_stamp_all(const ParticleArgs& a, cudaStream_t s)
 
 cudaError_t prepare_particle_kernels(int pair_cap)
 {
-    return cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(unsigned long long) * (size_t)pair_cap));
+    const int bytes = (int)(sizeof(unsigned long long) * (size_t)pair_cap);
+    cudaError_t e = cudaFuncSetAttribute(k_resolve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_resolve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace lbmp

@@ -16,11 +16,24 @@
 #include <type_traits>
 #include <utility>
 
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace lbmp {
 
 constexpr int SWEEP_THREADS = 128;
+
+// Arguments of the simulation a block works on: the kernel parameter for a single context,
+// entry blockIdx.y of a device array for a batch of cells.
+template <bool B, class A>
+__device__ __forceinline__ A pick_args(const A& a0, const A* __restrict__ cells)
+{
+    if constexpr (B)
+        return cells[blockIdx.y];
+    else
+        return a0;
+}
 
 template <int I, int N, class F>
 __device__ __forceinline__ void sfor(F&& f)
@@ -436,9 +449,11 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
 
 // Rebuilds the IS-source masks at the sites of the listed particles (their site sets hold
 // every site whose mask can be non-zero or can have changed).
-template <class L>
-__global__ void k_update_masks(const MaskArgs a)
+template <class L, bool B>
+__global__ void k_update_masks(const MaskArgs a0, const MaskArgs* __restrict__ cells)
 {
+    const MaskArgs a = pick_args<B>(a0, cells);
+    if (a.np == 0 || (a.list && !a.cnt)) return;
     const int count = a.list ? a.cnt->nrestamp : a.np;
     const Geom& g = a.g;
     for (int b = blockIdx.x; b < count; b += gridDim.x) {
@@ -624,6 +639,38 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
     sweep_site<L, S, WALLS, PART>(a, x, y, z, idx, valid, n, f, tagx, mask);
 }
 
+// One launch over a batch of cells: each block takes tiles of the schedule table (one, or a
+// stride of them in the persistent form) and runs the same per-site step as k_sweep with the
+// arguments of the tile's cell.
+template <class L, typename S, bool WALLS, bool PART>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep_batch(const BatchSweepArgs b)
+{
+    using C = typename Store<S>::C;
+    constexpr int Q = L::Q;
+    for (int e = blockIdx.x; e < b.ntiles; e += gridDim.x) {
+        const int4 t = b.table[e];
+        const SweepArgs a = b.cells[t.x];
+        const Geom& g = a.g;
+        const int lw = t.z >> 16;
+        const int xr = t.y + (int)(threadIdx.x & ((1u << lw) - 1u));
+        const int yr = (t.z & 0xFFFF) + (int)(threadIdx.x >> lw);
+        const bool valid = xr < g.nx && yr < g.ny;
+        const int x = min(xr, g.nx - 1), y = min(yr, g.ny - 1), z = t.w;
+        const unsigned idx = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
+        const Nbr n = neighbours<WALLS>(g, x, y, z);
+        unsigned tagx = TAG_FLUID, mask = 0;
+        if constexpr (PART) {
+            if (a.pv.tag != nullptr) {
+                tagx = a.pv.tag[idx];
+                mask = a.pv.ismask[idx];
+            }
+        }
+        C f[Q];
+        pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
+        sweep_site<L, S, WALLS, PART>(a, x, y, z, idx, valid, n, f, tagx, mask);
+    }
+}
+
 template <class L, typename S, bool WALLS>
 __global__ void k_materialize(const MaterializeArgs a)
 {
@@ -761,11 +808,13 @@ __global__ void k_fill_rest(S* dst, unsigned N)
 
 // Post-collision density at the new IS sites of particles whose shift changed (their IS
 // sites may not have been IS, hence not saved, during the sweep).
-template <class L, typename S>
-__global__ void k_stash_fix(const StashFixArgs a)
+template <class L, typename S, bool B>
+__global__ void k_stash_fix(const StashFixArgs a0, const StashFixArgs* __restrict__ cells)
 {
     using St = Store<S>;
     using C = typename St::C;
+    const StashFixArgs a = pick_args<B>(a0, cells);
+    if (!a.cnt) return;
     const int nlist = a.cnt->nchanged;
     const size_t N = a.g.N;
     const S* fout = (const S*)a.fout;
@@ -855,23 +904,73 @@ void launch_fill_rest(int lattice, void* dst, unsigned N, cudaStream_t s)
 template <typename S>
 void launch_stash_fix(const StashFixArgs& a, cudaStream_t s)
 {
-    if (a.lattice == 0) k_stash_fix<D2Q9, S><<<256, 128, 0, s>>>(a);
-    else k_stash_fix<D3Q19, S><<<256, 128, 0, s>>>(a);
+    if (a.lattice == 0) k_stash_fix<D2Q9, S, false><<<256, 128, 0, s>>>(a, nullptr);
+    else k_stash_fix<D3Q19, S, false><<<256, 128, 0, s>>>(a, nullptr);
 }
 
 template <typename S>
 void launch_update_masks(const MaskArgs& a, cudaStream_t s)
 {
-    if (a.lattice == 0) k_update_masks<D2Q9><<<304, 128, 0, s>>>(a);
-    else k_update_masks<D3Q19><<<304, 128, 0, s>>>(a);
+    if (a.lattice == 0) k_update_masks<D2Q9, false><<<304, 128, 0, s>>>(a, nullptr);
+    else k_update_masks<D3Q19, false><<<304, 128, 0, s>>>(a, nullptr);
+}
+
+// Batched forms (one lattice for every cell of a batch).
+template <typename S>
+void launch_stash_fix_batch(int lattice, const StashFixArgs* cells, int nc, cudaStream_t s)
+{
+    const dim3 grid(std::max(2, 256 / nc), nc);
+    if (lattice == 0) k_stash_fix<D2Q9, S, true><<<grid, 128, 0, s>>>(StashFixArgs{}, cells);
+    else k_stash_fix<D3Q19, S, true><<<grid, 128, 0, s>>>(StashFixArgs{}, cells);
+}
+
+template <typename S>
+void launch_update_masks_batch(int lattice, const MaskArgs* cells, int nc, cudaStream_t s)
+{
+    const dim3 grid(std::max(2, 304 / nc), nc);
+    if (lattice == 0) k_update_masks<D2Q9, true><<<grid, 128, 0, s>>>(MaskArgs{}, cells);
+    else k_update_masks<D3Q19, true><<<grid, 128, 0, s>>>(MaskArgs{}, cells);
+}
+
+template <class L, typename S, bool WALLS, bool PART>
+void launch_sweep_batch_v(const BatchSweepArgs& b, cudaStream_t s)
+{
+    const unsigned grid = b.grid > 0 ? (unsigned)b.grid : (unsigned)b.ntiles;
+    k_sweep_batch<L, S, WALLS, PART><<<grid, SWEEP_THREADS, 0, s>>>(b);
+}
+
+template <class L, typename S>
+void launch_sweep_batch_l(const BatchSweepArgs& b, cudaStream_t s)
+{
+    if (b.walls && b.part) launch_sweep_batch_v<L, S, true, true>(b, s);
+    else if (b.walls) launch_sweep_batch_v<L, S, true, false>(b, s);
+    else if (b.part) launch_sweep_batch_v<L, S, false, true>(b, s);
+    else launch_sweep_batch_v<L, S, false, false>(b, s);
+}
+
+template <typename S>
+void launch_sweep_batch(const BatchSweepArgs& b, cudaStream_t s)
+{
+    if (b.ntiles == 0) return;
+    if (b.lattice == 0) launch_sweep_batch_l<D2Q9, S>(b, s);
+    else launch_sweep_batch_l<D3Q19, S>(b, s);
 }
 
 template <typename S>
 const KernelTable* make_table()
 {
-    static const KernelTable t = {launch_sweep<S>,     launch_update_masks<S>, launch_materialize<S>, launch_convert_in<S>,
-                                  launch_unstream<S>,  launch_fill_rest<S>,   launch_stash_fix<S>,
-                                  (int)sizeof(S),      (int)sizeof(typename Store<S>::C)};
+    static const KernelTable t = {launch_sweep<S>,
+                                  launch_update_masks<S>,
+                                  launch_materialize<S>,
+                                  launch_convert_in<S>,
+                                  launch_unstream<S>,
+                                  launch_fill_rest<S>,
+                                  launch_stash_fix<S>,
+                                  launch_sweep_batch<S>,
+                                  launch_stash_fix_batch<S>,
+                                  launch_update_masks_batch<S>,
+                                  (int)sizeof(S),
+                                  (int)sizeof(typename Store<S>::C)};
     return &t;
 }
 

@@ -26,7 +26,13 @@ LBM_PERIODIC, LBM_NOSLIP = 0, 1
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
             "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_bs_exchange_noalloc",
-            "lbm_last_error", "lbm_destroy")
+            "lbm_last_error", "lbm_destroy",
+            "lbm_batch_create", "lbm_batch_add_particles", "lbm_batch_cell", "lbm_batch_set_tuning",
+            "lbm_batch_step", "lbm_batch_synchronize", "lbm_batch_profile_steps", "lbm_batch_get_info",
+            "lbm_batch_stream", "lbm_schedule_tiles", "lbm_batch_last_error", "lbm_batch_destroy")
+# entry points whose return value is not an lbm_status
+_NOT_STATUS = ("lbm_last_error", "lbm_destroy", "lbm_batch_cell", "lbm_batch_stream", "lbm_schedule_tiles",
+               "lbm_batch_last_error", "lbm_batch_destroy")
 
 
 class LbmError(RuntimeError):
@@ -67,8 +73,25 @@ def load(path: str = LIB_PATH):
     lib.lbm_last_error.argtypes = [P]
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_destroy.argtypes = [P]
+    lib.lbm_batch_create.argtypes = [ctypes.POINTER(P), i32, i32, I, D, D, i32, I, D, ctypes.c_double, i32]
+    lib.lbm_batch_add_particles.argtypes = [P, i32, i32, D, D, D, D, D]
+    lib.lbm_batch_cell.argtypes = [P, i32]
+    lib.lbm_batch_cell.restype = P
+    lib.lbm_batch_set_tuning.argtypes = [P, I, i32, i32, i32]
+    lib.lbm_batch_step.argtypes = [P, i32]
+    lib.lbm_batch_synchronize.argtypes = [P]
+    lib.lbm_batch_profile_steps.argtypes = [P, i32, D]
+    lib.lbm_batch_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbm_batch_stream.argtypes = [P]
+    lib.lbm_batch_stream.restype = P
+    lib.lbm_schedule_tiles.argtypes = [i32, I, I, i32, I]
+    lib.lbm_schedule_tiles.restype = ctypes.c_longlong
+    lib.lbm_batch_last_error.argtypes = [P]
+    lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    lib.lbm_batch_destroy.argtypes = [P]
+    lib.lbm_batch_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("lbm_last_error", "lbm_destroy"):
+        if name not in _NOT_STATUS:
             getattr(lib, name).restype = ctypes.c_int
     lib.lbm_destroy.restype = None
     _lib = lib
@@ -211,8 +234,118 @@ def lbm_destroy(h):
         load().lbm_destroy(h)
 
 
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _bcheck(b, status):
+    if status != LBM_OK:
+        msg = load().lbm_batch_last_error(b) if b else b"(no batch)"
+        raise LbmError(status, msg.decode(errors="replace") if msg else "")
+
+
+def lbm_batch_create(lattice, dims, taus, body_forces=None, precision=LBM_FP32, faces=None, particle_gravity=None,
+                     contact_gap=0.0, body_force_on_particles=False):
+    lib = load()
+    d = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 3)
+    n = d.shape[0]
+    t = _f64(taus, n)
+    F = None if body_forces is None else _f64(body_forces).reshape(n, 3)
+    fa = None if faces is None else np.ascontiguousarray(faces, dtype=np.int32).reshape(6)
+    g = _f64(particle_gravity, 3)
+    h = ctypes.c_void_p()
+    st = lib.lbm_batch_create(ctypes.byref(h), int(lattice), n, _ip(d), _dp(t), _dp(F), int(precision), _ip(fa), _dp(g),
+                              float(contact_gap), int(bool(body_force_on_particles)))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_batch_create(%d cells)" % n)
+    return h
+
+
+def lbm_batch_add_particles(b, cell, centers, radii, densities, velocities=None, omegas=None):
+    c = _f64(centers).reshape(-1, 3)
+    n = c.shape[0]
+    r = _f64(radii, n)
+    d = _f64(densities, n)
+    v = None if velocities is None else _f64(velocities).reshape(n, 3)
+    o = None if omegas is None else _f64(omegas).reshape(n, 3)
+    _bcheck(b, load().lbm_batch_add_particles(b, int(cell), n, _dp(c), _dp(r), _dp(d), _dp(v), _dp(o)))
+
+
+def lbm_batch_cell(b, cell):
+    h = load().lbm_batch_cell(b, int(cell))
+    if not h:
+        raise IndexError(cell)
+    return ctypes.c_void_p(h)
+
+
+def lbm_batch_set_tuning(b, tile_width=None, order=0, grid=0, steps_per_graph=1):
+    tw = None if tile_width is None else np.ascontiguousarray(tile_width, dtype=np.int32)
+    _bcheck(b, load().lbm_batch_set_tuning(b, _ip(tw), int(order), int(grid), int(steps_per_graph)))
+
+
+def lbm_batch_step(b, n=1):
+    _bcheck(b, load().lbm_batch_step(b, int(n)))
+
+
+def lbm_batch_synchronize(b):
+    _bcheck(b, load().lbm_batch_synchronize(b))
+
+
+def lbm_batch_profile_steps(b, n):
+    out = np.zeros(3)
+    _bcheck(b, load().lbm_batch_profile_steps(b, int(n), _dp(out)))
+    return {"sweep_ms": float(out[0]), "particle_ms": float(out[1]), "step_ms": float(out[2])}
+
+
+def lbm_batch_get_info(b):
+    out = (ctypes.c_longlong * 5)()
+    _bcheck(b, load().lbm_batch_get_info(b, out))
+    return dict(zip(("cells", "sites", "particles", "tiles", "launches_per_step"), list(out)))
+
+
+def lbm_batch_stream(b):
+    return load().lbm_batch_stream(b)
+
+
+def lbm_schedule_tiles(dims, tile_width=None, order=0):
+    """Sweep schedule of a batch (host-only): int32 array [tiles, 4] of (cell, x0,
+    y0 | log2(width) << 16, z) in launch order."""
+    d = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 3)
+    tw = None if tile_width is None else np.ascontiguousarray(tile_width, dtype=np.int32)
+    lib = load()
+    n = lib.lbm_schedule_tiles(d.shape[0], _ip(d), _ip(tw), int(order), None)
+    if n < 0:
+        raise ValueError("lbm_schedule_tiles: bad argument")
+    out = np.zeros((n, 4), dtype=np.int32)
+    lib.lbm_schedule_tiles(d.shape[0], _ip(d), _ip(tw), int(order), _ip(out))
+    return out
+
+
+def lbm_batch_last_error(b):
+    m = load().lbm_batch_last_error(b)
+    return m.decode(errors="replace") if m else ""
+
+
+def lbm_batch_destroy(b):
+    if b:
+        load().lbm_batch_destroy(b)
+
+
 class Simulation:
     """A context handle plus numpy-shaped getters (lattice 0 = D2Q9, 1 = D3Q19)."""
+
+    @classmethod
+    def borrowed(cls, handle, lattice, nx, ny, nz, np_):
+        """A view of a context owned elsewhere (a cell of a Batch): never destroyed here."""
+        s = cls.__new__(cls)
+        s.lattice = lattice
+        s.Q = 9 if lattice == LBM_D2Q9 else 19
+        s.shape = (nz, ny, nx)
+        s.N = nx * ny * nz
+        s.h = handle
+        s.np = np_
+        s._owned = False
+        return s
 
     def __init__(self, lattice, nx, ny, nz, tau, body_force=(0.0, 0.0, 0.0), precision="fp32",
                  walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False,
@@ -233,10 +366,12 @@ class Simulation:
             self.h = None
             raise
         self.np = 0
+        self._owned = True
 
     def close(self):
         if getattr(self, "h", None):
-            lbm_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lbm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -277,3 +412,55 @@ class Simulation:
 
     def profile(self, n):
         return lbm_profile_steps(self.h, n)
+
+
+class Batch:
+    """An ensemble of independent cells stepped together (lbm_batch_*)."""
+
+    def __init__(self, lattice, dims, taus, body_forces=None, precision="fp32", walls=(0, 0, 0),
+                 gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False):
+        self.lattice = lattice
+        self.dims = [tuple(int(v) for v in d) for d in np.asarray(dims).reshape(-1, 3)]
+        faces = [LBM_NOSLIP if walls[k // 2] else LBM_PERIODIC for k in range(6)]
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.h = lbm_batch_create(lattice, self.dims, taus, body_forces, prec, faces, gravity, gap,
+                                  body_force_on_particles)
+        self.np = [0] * len(self.dims)
+
+    def __len__(self):
+        return len(self.dims)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def add_particles(self, cell, centers, radii, densities, velocities=None, omegas=None):
+        lbm_batch_add_particles(self.h, cell, centers, radii, densities, velocities, omegas)
+        self.np[cell] = lbm_get_info(lbm_batch_cell(self.h, cell))["particles"]
+
+    def cell(self, i):
+        nx, ny, nz = self.dims[i]
+        return Simulation.borrowed(lbm_batch_cell(self.h, i), self.lattice, nx, ny, nz, self.np[i])
+
+    def set_tuning(self, tile_width=None, order=0, grid=0, steps_per_graph=1):
+        lbm_batch_set_tuning(self.h, tile_width, order, grid, steps_per_graph)
+
+    def step(self, n=1):
+        lbm_batch_step(self.h, n)
+
+    def synchronize(self):
+        lbm_batch_synchronize(self.h)
+
+    def profile(self, n):
+        return lbm_batch_profile_steps(self.h, n)
+
+    def info(self):
+        return lbm_batch_get_info(self.h)
+
+    @property
+    def stream(self):
+        return lbm_batch_stream(self.h)

@@ -218,3 +218,77 @@ def suspension_3d_scaled(n: int, seed=3) -> Workload:
     """The 512^3 suspension scaled to n^3 with the same solid fraction and sphere size."""
     n_particles = max(1, int(round(16000 * (n / 512.0) ** 3)))
     return suspension_3d(n, n_particles, 8.0, seed)
+
+
+@dataclass
+class Ensemble:
+    """Independent periodic D3Q19 cells of uneven sizes, each with a few spheres."""
+
+    name: str
+    dims: list                   # [(nx, ny, nz)] per cell
+    taus: list
+    centers: list                # per cell: [n_k, 3]
+    radii: list                  # per cell: [n_k]
+    densities: list
+    velocities: list
+    dropped: list                # spheres of the draw that did not fit, per cell
+    body_force: tuple = (1e-6, 0.0, 0.0)
+    body_force_on_particles: bool = True
+    steps: int = 500
+    precision: str = "fp32"
+
+    @property
+    def sites(self) -> int:
+        return int(sum(int(a) * int(b) * int(c) for a, b, c in self.dims))
+
+    @property
+    def n_particles(self) -> int:
+        return int(sum(len(r) for r in self.radii))
+
+
+def _place_spheres(dims, radii, g, min_gap=1.0, attempts=10_000):
+    """Random sequential addition in a periodic box: each sphere takes the first of
+    `attempts` uniform candidate centres that keeps a surface gap >= min_gap to the spheres
+    already placed (minimum image); a sphere with no such candidate is dropped."""
+    L = np.asarray(dims, dtype=np.float64)
+    placed_c, placed_r, dropped = [], [], 0
+    for r in radii:
+        cand = g.uniform(0.0, 1.0, size=(attempts, 3)) * L
+        ok = np.ones(attempts, dtype=bool)
+        for c, rr in zip(placed_c, placed_r):
+            d = cand - c
+            d -= L * np.floor(d / L + 0.5)
+            ok &= (d * d).sum(1) >= (r + rr + min_gap) ** 2
+        idx = np.flatnonzero(ok)
+        if idx.size == 0:
+            dropped += 1
+            continue
+        placed_c.append(cand[idx[0]])
+        placed_r.append(float(r))
+    c = np.asarray(placed_c, dtype=np.float64).reshape(-1, 3)
+    return c, np.asarray(placed_r, dtype=np.float64), dropped
+
+
+def ensemble_cells(n_cells=64, seed=4, edge=(32, 128), spheres=(1, 8), radius=(4.0, 10.0),
+                   tau=(0.55, 1.0), density_ratio=1.2, velocity_sigma=1e-3) -> Ensemble:
+    """Batched-ensemble workload: n_cells periodic cells, each edge drawn independently and
+    uniformly from the integers edge[0]..edge[1], a uniform integer number of spheres in
+    spheres[0]..spheres[1] with radii uniform in radius (placed by random sequential
+    addition, min gap 1; spheres that do not fit after 10^4 attempts are dropped and
+    counted), tau uniform in the given range, velocities N(0, velocity_sigma^2), density
+    ratio 1.2, body force 1e-6 along x on fluid and particles, FP32, 500 steps."""
+    g = rng(seed)
+    dims = [tuple(int(v) for v in g.integers(edge[0], edge[1] + 1, size=3)) for _ in range(n_cells)]
+    taus = [float(v) for v in g.uniform(tau[0], tau[1], size=n_cells)]
+    cs, rs, ds, vs, drop = [], [], [], [], []
+    for k in range(n_cells):
+        gk = rng(seed * 1000 + 17 + k)
+        n = int(gk.integers(spheres[0], spheres[1] + 1))
+        r = gk.uniform(radius[0], radius[1], size=n)
+        c, rr, dropped = _place_spheres(dims[k], r, gk)
+        cs.append(c)
+        rs.append(rr)
+        ds.append(np.full(len(rr), float(density_ratio)))
+        vs.append(gk.normal(0.0, velocity_sigma, size=(len(rr), 3)))
+        drop.append(dropped)
+    return Ensemble("d3q19_ensemble_%dcells_edge%d-%d" % (n_cells, edge[0], edge[1]), dims, taus, cs, rs, ds, vs, drop)
