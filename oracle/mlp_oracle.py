@@ -1,0 +1,95 @@
+"""FP64 reference of the learned drag / torque closure network.
+
+TEST INFRASTRUCTURE ONLY: the plain, slow reference that the CUDA training and inference
+kernels are checked against. Only tests/, the smoke check and the benchmark's baseline legs
+may import it.
+
+The network is a multilayer perceptron x -> relu(W1 x + b1) -> relu(W2 h1 + b2) -> W3 h2 + b3
+trained by mean-squared error with Adam (Kingma & Ba, 2015: m <- b1 m + (1 - b1) g,
+v <- b2 v + (1 - b2) g^2, p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)). The
+CUDA path stores weights and activations in bfloat16 and accumulates in FP32; with
+``bf16=True`` this reference rounds the same quantities to bfloat16 at the same points (the
+inputs, the weights, the hidden activations and the back-propagated activation gradients)
+and computes everything else in FP64, so the two differ only by accumulation order and
+precision. The paper has no network; this closure is an addition outside it.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64. bfloat16 keeps the
+    top 16 bits of an IEEE binary32 value; inputs are first rounded to binary32."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    nan = np.isnan(a)
+    out = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    out[nan] = np.nan
+    return out
+
+
+def init_params(sizes, seed):
+    """He-uniform weights (bound sqrt(6 / fan_in)) and zero biases for layer widths `sizes`
+    (e.g. [256, 128, 128, 6]); W[l] has shape (sizes[l+1], sizes[l])."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    p = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        bound = np.sqrt(6.0 / a)
+        p.append([g.uniform(-bound, bound, size=(b, a)), np.zeros(b)])
+    return p
+
+
+def _q(x, bf16):
+    return bf16_round(x) if bf16 else np.asarray(x, dtype=np.float64)
+
+
+def forward(params, X, bf16=False):
+    """Returns (Y, cache). X: (B, K). Hidden layers use relu; the last layer is linear."""
+    h = _q(X, bf16)
+    cache = [h]
+    L = len(params)
+    for l, (W, b) in enumerate(params):
+        z = h @ _q(W, bf16).T + b
+        if l < L - 1:
+            h = _q(np.maximum(z, 0.0), bf16)
+            cache.append(h)
+        else:
+            h = z
+    return h, cache
+
+
+def loss_and_grads(params, X, T, bf16=False):
+    """Mean-squared error over all B x O outputs, and its gradient for every W and b."""
+    Y, cache = forward(params, X, bf16)
+    B, O = Y.shape
+    R = Y - T
+    loss = float(np.sum(R * R) / (B * O))
+    d = 2.0 * R / (B * O)
+    grads = [None] * len(params)
+    for l in range(len(params) - 1, -1, -1):
+        W, _ = params[l]
+        dq = _q(d, bf16)  # the CUDA path keeps each layer's output gradient in bfloat16
+        grads[l] = [dq.T @ cache[l], dq.sum(0)]
+        if l > 0:
+            d = (dq @ _q(W, bf16)) * (cache[l] > 0.0)
+    return loss, grads
+
+
+def adam_init(params):
+    return [[np.zeros_like(W), np.zeros_like(b)] for W, b in params], [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
+
+
+def adam_step(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (step number t >= 1), in place on params, m, v."""
+    c1 = 1.0 - beta1 ** t
+    c2 = 1.0 - beta2 ** t
+    for l in range(len(params)):
+        for k in range(2):
+            g = grads[l][k]
+            m[l][k] = beta1 * m[l][k] + (1.0 - beta1) * g
+            v[l][k] = beta2 * v[l][k] + (1.0 - beta2) * g * g
+            params[l][k] = params[l][k] - lr * (m[l][k] / c1) / (np.sqrt(v[l][k] / c2) + eps)
+    return params
