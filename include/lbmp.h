@@ -279,6 +279,58 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 /* Destroys the batch and all of its cells (NULL is a no-op). */
 void lbm_batch_destroy(lbm_batch* b);
 
+/* Inputs of the learned closure for every particle of ctx, enqueued on the context's stream:
+ * the moments (rho - 1, u - u_p) / u_ref at the n_side^3 nodes x_p + spacing (i - (n_side-1)/2,
+ * j - .., k - ..), trilinearly interpolated from the 8 surrounding sites of the current state
+ * (periodic axes wrap, walled axes clamp to the domain; u as lbm_get_fields). out: device
+ * pointer to np * n_side^3 * 4 floats, [p][(k n_side + j) n_side + i][4]. D2Q9: nodes that
+ * differ only in k carry the same values.
+ * Errors: LBM_E_INVALID (n_side outside 1..8, spacing <= 0, u_ref zero or not finite). */
+lbm_status lbm_closure_features(lbm_ctx* ctx, int n_side, double spacing, double u_ref, float* out);
+
+/* ---- Learned drag / torque closure network -------------------------------------------------
+ * Not in the paper: a multilayer perceptron x -> relu(W1 x + b1) -> ... -> W_L h + b_L that
+ * predicts the correction to the force and torque a coarse-resolution particle feels. It is
+ * trained and evaluated on the GPU: weights and activations in bfloat16, tensor-core products
+ * accumulated in FP32, FP32 master weights, Adam (Kingma & Ba 2015) and a mean-squared-error
+ * loss. Parameters are laid out layer by layer, W_l (sizes[l+1] x sizes[l], row-major) then
+ * b_l. Data arrays are caller-owned device pointers (FP32, row-major); every call enqueues on
+ * the stream given at creation and returns after enqueueing unless it returns host values. */
+typedef struct lbm_mlp lbm_mlp;
+
+/* nlayers (1..8) weight layers of widths sizes[0..nlayers] (each 1..4096). Parameters start at
+ * zero (set them with lbm_mlp_set_params). Errors: LBM_E_INVALID, LBM_E_CUDA, LBM_E_OOM. */
+lbm_status lbm_mlp_create(lbm_mlp** out, int nlayers, const int* sizes, void* cuda_stream);
+
+/* Number of parameters (weights and biases), or -1 for NULL. */
+long long lbm_mlp_num_params(const lbm_mlp* net);
+
+/* Host FP64 parameters in (rounded to FP32 masters and bfloat16 copies); resets Adam. */
+lbm_status lbm_mlp_set_params(lbm_mlp* net, const double* params);
+
+/* Host copies of the FP32 masters and / or of the last gradients (either may be NULL). */
+lbm_status lbm_mlp_get_params(lbm_mlp* net, double* params, double* grads);
+
+/* y[rows][sizes[L]] = network(x[rows][sizes[0]]) (device pointers). */
+lbm_status lbm_mlp_forward(lbm_mlp* net, const float* x, int rows, float* y);
+
+/* Mean-squared error of the network on (x, t) over all rows x outputs, and its gradient
+ * (kept for lbm_mlp_adam_step / lbm_mlp_get_params); *loss (host, may be NULL) receives
+ * the loss, which synchronizes. */
+lbm_status lbm_mlp_loss_grad(lbm_mlp* net, const float* x, const float* t, int rows, double* loss);
+
+/* One Adam step with the last gradients. */
+lbm_status lbm_mlp_adam_step(lbm_mlp* net, double lr, double beta1, double beta2, double eps);
+
+/* Trains on n rows (x, t) for `epochs` epochs of shuffled minibatches of `batch` rows (the
+ * shuffle is seeded; a last partial minibatch is skipped), Adam with beta1 0.9, beta2 0.999,
+ * eps 1e-8. epoch_loss (host, may be NULL) receives the mean minibatch loss of each epoch. */
+lbm_status lbm_mlp_train(lbm_mlp* net, const float* x, const float* t, int n, int batch, int epochs, double lr,
+                         unsigned seed, double* epoch_loss);
+
+const char* lbm_mlp_last_error(const lbm_mlp* net);
+void lbm_mlp_destroy(lbm_mlp* net);
+
 /* Description of the last non-OK status of ctx (static storage; never NULL). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

@@ -93,3 +93,43 @@ def adam_step(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
             v[l][k] = beta2 * v[l][k] + (1.0 - beta2) * g * g
             params[l][k] = params[l][k] - lr * (m[l][k] / c1) / (np.sqrt(v[l][k] / c2) + eps)
     return params
+
+
+def stencil_features(rho, u, centers, up, n_side, h, u_ref, walls=(0, 0, 0)):
+    """Closure inputs written out: for each particle p and node (i, j, k) of an n_side^3
+    stencil at x_p + h (i - (n_side - 1)/2, ...), the trilinear interpolation of (rho - 1, u)
+    from the 8 surrounding lattice sites (periodic axes wrap, walled axes clamp), minus the
+    particle velocity for u, divided by u_ref. rho: (nz, ny, nx); u: (nz, ny, nx, 3).
+    Returns (np, n_side^3 * 4), nodes in (k, j, i) order, 4 values per node."""
+    nz, ny, nx = rho.shape
+    dims = (nx, ny, nz)
+    D = 2 if nz == 1 else 3
+    out = np.zeros((len(centers), n_side ** 3 * 4))
+    for p in range(len(centers)):
+        for k in range(n_side):
+            for j in range(n_side):
+                for i in range(n_side):
+                    ijk = (i, j, k)
+                    lo, hi, w1 = [0, 0, 0], [0, 0, 0], [0.0, 0.0, 0.0]
+                    for a in range(D):
+                        pos = centers[p][a] + h * (ijk[a] - 0.5 * (n_side - 1))
+                        f = np.floor(pos)
+                        w1[a] = pos - f
+                        a0, a1 = int(f), int(f) + 1
+                        if walls[a]:
+                            a0, a1 = min(max(a0, 0), dims[a] - 1), min(max(a1, 0), dims[a] - 1)
+                        else:
+                            a0, a1 = a0 % dims[a], a1 % dims[a]
+                        lo[a], hi[a] = a0, a1
+                    acc = np.zeros(4)
+                    for c in range(8 if D == 3 else 4):
+                        s = [hi[a] if (c >> a) & 1 else lo[a] for a in range(3)]
+                        w = 1.0
+                        for a in range(D):
+                            w *= w1[a] if (c >> a) & 1 else 1.0 - w1[a]
+                        acc[0] += w * (rho[s[2], s[1], s[0]] - 1.0)
+                        acc[1:] += w * u[s[2], s[1], s[0]]
+                    q = (k * n_side + j) * n_side + i
+                    out[p, 4 * q] = acc[0] / u_ref
+                    out[p, 4 * q + 1:4 * q + 4] = (acc[1:] - up[p]) / u_ref
+    return out

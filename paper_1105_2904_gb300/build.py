@@ -1,10 +1,10 @@
 """Builds the CUDA library ``liblbmp.so`` in-tree for sm_103a (GB300).
 
-Six translation units are compiled in parallel with nvcc, one ``-gencode`` each:
+Seven translation units are compiled in parallel with nvcc, one ``-gencode`` each:
 ``api.cu`` (host C-ABI; host code with -ffp-contract=off), ``sweep_f64.cu`` and
 ``particles.cu`` (-fmad=false: FP64 arithmetic evaluated exactly as written),
 ``sweep_lp.cu`` (FP32 / FP16 / BF16 storage), ``noalloc.cu`` (the allocation-free boundary-site
-exchange), ``batch.cu`` (batched ensembles). Output: ``paper_1105_2904_gb300/_lib/``.
+exchange), ``batch.cu`` (batched ensembles), ``mlp.cu`` (the closure network). Output: ``paper_1105_2904_gb300/_lib/``.
 """
 from __future__ import annotations
 
@@ -31,6 +31,7 @@ UNITS = {
     "sweep_lp.cu": [],
     "noalloc.cu": [],
     "batch.cu": [],
+    "mlp.cu": [],
 }
 
 

@@ -1,0 +1,155 @@
+"""Learned drag / torque closure for coarse-resolution particles (not in the paper).
+
+A coarse run resolves each sphere with radius r_c = 3 lattice units; a fine run of the same
+configuration uses radius 12 (a factor f = 4 finer lattice). With the same relaxation time in
+both, diffusive scaling makes them the same physical problem: the fine run takes f^2 steps
+per coarse step, its body-force acceleration is f^-3 of the coarse one, and forces in lattice
+units agree while torques carry a factor f (force unit rho dx^4 / dt^2, torque unit
+rho dx^5 / dt^2). A network trained on pairs of such runs predicts, from moments of the
+coarse flow around a sphere, the difference between the fine and the coarse force and
+torque. The coarse method without the network stays the fallback, and the fine method the
+judge of the error.
+
+Everything here is orchestration over the C-ABI: the runs, the stencil moments
+(lbm_closure_features), the training and the inference (lbm_mlp_*) run in the library's
+kernels; torch only holds device memory.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import lbmp
+from . import workloads as W
+
+SIZES = [256, 128, 128, 6]
+
+
+@dataclass
+class PairSpec:
+    """Coarse periodic cells of edge L with n fixed spheres of radius r driven by a body
+    force along x, observed after `steps` coarse steps; the fine twin is `factor` times
+    finer."""
+
+    L: int = 32
+    n_spheres: int = 8
+    r: float = 3.0
+    tau: float = 1.0
+    accel: float = 1e-5
+    steps: int = 200
+    factor: int = 4
+    min_gap: float = 2.0
+    n_side: int = 4
+    spacing: float = 4.0     # stencil node spacing (coarse lattice units)
+    precision: str = "fp32"
+
+
+def place(spec: PairSpec, n_cells: int, seed: int):
+    """Seeded sphere centres (random sequential addition, periodic, surface gap >= min_gap)."""
+    out = []
+    for k in range(n_cells):
+        g = W.rng(seed * 7919 + k)
+        c, r, dropped = W._place_spheres((spec.L,) * 3, np.full(spec.n_spheres, spec.r), g, spec.min_gap)
+        out.append(c)
+    return out
+
+
+def _run(spec: PairSpec, centers, fine: bool):
+    f = spec.factor if fine else 1
+    L = spec.L * f
+    n = len(centers)
+    b = lbmp.Batch(1, [(L, L, L)] * n, [spec.tau] * n, [(spec.accel / f ** 3, 0.0, 0.0)] * n,
+                   precision=spec.precision)
+    for k, c in enumerate(centers):
+        cc = c * f + 0.5 * (f - 1) if fine else c
+        b.add_particles(k, cc, np.full(len(c), spec.r * f), np.full(len(c), np.inf))
+    b.set_tuning(steps_per_graph=50)
+    b.step(spec.steps * f * f)
+    b.synchronize()
+    return b
+
+
+def generate(spec: PairSpec, n_cells: int, seed: int):
+    """One batch of coarse / fine pairs. Returns (features [N, 256] CUDA tensor,
+    targets [N, 6], coarse [N, 6], fine [N, 6], scale [N, 2]) with N = spheres of all cells;
+    force rows are (Fx, Fy, Fz, Tx, Ty, Tz), the fine torque already scaled to coarse units;
+    targets are (fine - coarse) divided by the Stokes scales 6 pi nu r U and 6 pi nu r^2 U,
+    U the cell's mean fluid velocity along x (scale holds both)."""
+    import torch
+
+    centers = place(spec, n_cells, seed)
+    nu = (spec.tau - 0.5) / 3.0
+    bc = _run(spec, centers, fine=False)
+    feats, coarse, scales = [], [], []
+    for k in range(n_cells):
+        cell = bc.cell(k)
+        rho, u = cell.get_fields()
+        tags = cell.get_tags()
+        U = float(u[..., 0][tags == 0xFFFFFFFF].mean())
+        feats.append(cell.closure_features(spec.n_side, spec.spacing, U))
+        p = cell.get_particles()
+        coarse.append(np.concatenate([p["force"], p["torque"]], axis=1))
+        s_f = 6.0 * math.pi * nu * spec.r * U
+        scales.append(np.tile([s_f, s_f * spec.r], (len(centers[k]), 1)))
+    bc.close()
+    bf = _run(spec, centers, fine=True)
+    fine = []
+    for k in range(n_cells):
+        p = bf.cell(k).get_particles()
+        fine.append(np.concatenate([p["force"], p["torque"] / spec.factor], axis=1))
+    bf.close()
+    X = torch.cat(feats, 0)
+    coarse = np.concatenate(coarse, 0)
+    fine = np.concatenate(fine, 0)
+    scale = np.concatenate(scales, 0)
+    S = np.repeat(scale, 3, axis=1)
+    T = (fine - coarse) / S
+    return X, T, coarse, fine, scale
+
+
+class Closure:
+    """The trained network with its output normalisation."""
+
+    def __init__(self, sizes=SIZES, seed=0):
+        self.sizes = list(sizes)
+        self.net = lbmp.MLP(self.sizes)
+        self.net.set_params(_he_init(self.sizes, seed))
+        self.mu = np.zeros(self.sizes[-1])
+        self.sd = np.ones(self.sizes[-1])
+
+    def close(self):
+        self.net.close()
+
+    def fit(self, X, T, epochs=300, batch=256, lr=1e-3, seed=0):
+        """Trains on features X (CUDA tensor) and targets T (numpy [N, 6]) normalised per
+        output; returns the per-epoch losses."""
+        import torch
+
+        self.mu = T.mean(0)
+        self.sd = T.std(0) + 1e-12
+        Tn = torch.tensor((T - self.mu) / self.sd, dtype=torch.float32, device=X.device)
+        return self.net.train(X, Tn, batch=batch, epochs=epochs, lr=lr, seed=seed)
+
+    def predict(self, X):
+        """Predicted targets (denormalised), numpy [N, 6]."""
+        return self.net.forward(X).cpu().double().numpy() * self.sd + self.mu
+
+    def corrected(self, X, coarse, scale):
+        """Coarse force and torque plus the predicted correction."""
+        return coarse + self.predict(X) * np.repeat(scale, 3, axis=1)
+
+
+def _he_init(sizes, seed):
+    g = W.rng(seed)
+    out = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        bound = math.sqrt(6.0 / a)
+        out.append([g.uniform(-bound, bound, size=(b, a)), np.zeros(b)])
+    return out
+
+
+def drag_errors(pred, fine):
+    """Relative error of the drag (x force) against the fine method."""
+    return np.abs(pred[:, 0] - fine[:, 0]) / np.abs(fine[:, 0])

@@ -736,6 +736,32 @@ static lbm_status materialize(lbm_ctx* ctx, int mode, double* out_a, double* out
     return LBM_OK;
 }
 
+lbm_status lbm_closure_features(lbm_ctx* ctx, int n_side, double spacing, double u_ref, float* out)
+{
+    if (!ctx || !out || n_side < 1 || n_side > 8 || !(spacing > 0.0) || !(u_ref != 0.0) || !std::isfinite(u_ref))
+        return LBM_E_INVALID;
+    if (ctx->np == 0) return LBM_OK;
+    CS(ensure_alloc(ctx));
+    FeatureArgs f{};
+    f.m.lattice = ctx->lattice;
+    f.m.g = ctx->g;
+    f.m.fin = ctx->f[ctx->cur];
+    f.m.pv = part_view(ctx);
+    f.m.stash_in = ctx->stash[ctx->cur];
+    for (int k = 0; k < 3; ++k) f.m.F[k] = ctx->F[k];
+    wall_args(ctx, f.m);
+    f.x = ctx->x;
+    f.pk = ctx->pk;
+    f.np = ctx->np;
+    f.n_side = n_side;
+    f.h = spacing;
+    f.u_ref = u_ref;
+    f.out = out;
+    ctx->kt->features(f, ctx->stream);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
 lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u)
 {
     if (!ctx) return LBM_E_INVALID;

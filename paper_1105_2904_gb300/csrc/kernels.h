@@ -95,6 +95,18 @@ struct BatchSweepArgs {
     int grid;                  // 0: one block per tile; > 0: that many blocks stride over the table
 };
 
+// Inputs of the closure network: stencil moments around each particle (see k_features).
+struct FeatureArgs {
+    MaterializeArgs m;         // the state (buffer, particle view, stash, walls, F)
+    const double* x;           // [np][3] centres
+    const PKern* pk;           // particle velocities
+    int np;
+    int n_side;                // stencil nodes per axis
+    double h;                  // node spacing
+    double u_ref;              // velocity scale
+    float* out;                // [np][n_side^3][4]
+};
+
 struct KernelTable {
     void (*sweep)(const SweepArgs&, cudaStream_t);
     void (*update_masks)(const MaskArgs&, cudaStream_t);
@@ -107,6 +119,7 @@ struct KernelTable {
     // per-cell argument arrays on the device, blockIdx.y = cell
     void (*stash_fix_batch)(int lattice, const StashFixArgs* cells, int ncells, cudaStream_t);
     void (*update_masks_batch)(int lattice, const MaskArgs* cells, int ncells, cudaStream_t);
+    void (*features)(const FeatureArgs&, cudaStream_t);
     int elem_bytes;
     int compute_bytes;
 };

@@ -671,21 +671,18 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep_batch(const BatchSweepA
     }
 }
 
+// Populations of site idx at a step boundary (streamed, pending IS imposition and wall
+// momentum applied), in the storage's compute form: f, or g = f - w for deviation storage.
 template <class L, typename S, bool WALLS>
-__global__ void k_materialize(const MaterializeArgs a)
+__device__ __forceinline__ void site_pull(const MaterializeArgs& a, unsigned idx, typename Store<S>::C f[])
 {
     using St = Store<S>;
     using C = typename St::C;
-    constexpr int Q = L::Q;
-    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.count) return;
     const Geom& g = a.g;
-    const unsigned idx = a.s0 + t;
     const int x = (int)(idx % (unsigned)g.nx);
     const int y = (int)((idx / (unsigned)g.nx) % (unsigned)g.ny);
     const int z = (int)(idx / ((unsigned)g.nx * (unsigned)g.ny));
     const Nbr n = neighbours<WALLS>(g, x, y, z);
-    C f[Q];
     pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
     if (a.pv.tag != nullptr && a.pv.tag[idx] != TAG_FLUID && *a.pv.pending) {
         const unsigned m = a.pv.ismask[idx];
@@ -705,42 +702,105 @@ __global__ void k_materialize(const MaterializeArgs a)
                 wall_momentum<L, C, WALLS>(n, a.uw->u, f);
         }
     }
-    double fd[Q];
-    sfor<0, Q>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        fd[i] = St::deviation ? (double)f[i] + L::w(i) : (double)f[i];
-    });
-    if (a.mode == 1) {
+}
+
+// rho = sum f (Eq. 1) and u = (sum f c + F/2) / rho (Eq. 2 with the Guo half-force) of site
+// idx; deviation storage sums the deviations (rho = 1 + sum g).
+template <class L, typename S, bool WALLS>
+__device__ __forceinline__ void site_moments(const MaterializeArgs& a, unsigned idx, double& rho, double u[3])
+{
+    using C = typename Store<S>::C;
+    constexpr int Q = L::Q;
+    C f[Q];
+    site_pull<L, S, WALLS>(a, idx, f);
+    double j[3] = {0.0, 0.0, 0.0};
+    rho = 0.0;
+    sfor<0, Q>([&](auto ic) { rho += (double)f[decltype(ic)::value]; });
+    if constexpr (Store<S>::deviation) rho = 1.0 + rho;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
         sfor<0, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            a.out0[(size_t)i * a.count + t] = fd[i];
+            j[k] += (double)f[i] * (double)L::c(i, k);
+        });
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = (j[k] + 0.5 * a.F[k]) / rho;
+}
+
+template <class L, typename S, bool WALLS>
+__global__ void k_materialize(const MaterializeArgs a)
+{
+    constexpr int Q = L::Q;
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.count) return;
+    const unsigned idx = a.s0 + t;
+    if (a.mode == 1) {
+        typename Store<S>::C f[Q];
+        site_pull<L, S, WALLS>(a, idx, f);
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            a.out0[(size_t)i * a.count + t] = Store<S>::deviation ? (double)f[i] + L::w(i) : (double)f[i];
         });
         return;
     }
-    // rho = sum f (Eq. 1); rho u = sum f c + F/2 (Eq. 2 with the Guo half-force).
-    double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
-    if constexpr (St::deviation) {
-        double drho = 0.0;
-        sfor<0, Q>([&](auto ic) { drho += (double)f[decltype(ic)::value]; });
-        rho = 1.0 + drho;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            sfor<0, Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                j[k] += (double)f[i] * (double)L::c(i, k);
-            });
-    } else {
-        sfor<0, Q>([&](auto ic) { rho += fd[decltype(ic)::value]; });
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            sfor<0, Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                j[k] += fd[i] * (double)L::c(i, k);
-            });
-    }
+    double rho, u[3];
+    site_moments<L, S, WALLS>(a, idx, rho, u);
     a.out0[t] = rho;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) a.out1[(size_t)t * 3 + k] = (j[k] + 0.5 * a.F[k]) / rho;
+    for (int k = 0; k < 3; ++k) a.out1[(size_t)t * 3 + k] = u[k];
+}
+
+// Closure inputs: for particle p (blockIdx.x) and stencil node q (thread), the moments
+// (rho - 1, u - u_p) / u_ref trilinearly interpolated at x_p + h (i - (n-1)/2, j - ..,
+// k - ..), q = (k n + j) n + i, from the 8 surrounding sites (periodic axes wrap, walled
+// axes clamp to the domain). out[p][q][4].
+template <class L, typename S, bool WALLS>
+__global__ void k_features(const FeatureArgs f)
+{
+    const int p = blockIdx.x;
+    const int nn = f.n_side * f.n_side * f.n_side;
+    const int D = f.m.lattice == 0 ? 2 : 3;
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+        const int ii[3] = {q % f.n_side, (q / f.n_side) % f.n_side, q / (f.n_side * f.n_side)};
+        const Geom& g = f.m.g;
+        const int nax[3] = {g.nx, g.ny, g.nz};
+        int lo[3], hi[3];
+        double w1[3];
+        for (int k = 0; k < 3; ++k) {
+            if (k >= D) {
+                lo[k] = hi[k] = 0;
+                w1[k] = 0.0;
+                continue;
+            }
+            const double pos = f.x[(size_t)p * 3 + k] + f.h * ((double)ii[k] - 0.5 * (double)(f.n_side - 1));
+            const double fl = floor(pos);
+            w1[k] = pos - fl;
+            int a0 = (int)fl, a1 = a0 + 1;
+            if (g.wall[k]) {
+                a0 = min(max(a0, 0), nax[k] - 1);
+                a1 = min(max(a1, 0), nax[k] - 1);
+            } else {
+                a0 = ((a0 % nax[k]) + nax[k]) % nax[k];
+                a1 = ((a1 % nax[k]) + nax[k]) % nax[k];
+            }
+            lo[k] = a0;
+            hi[k] = a1;
+        }
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < (D == 3 ? 8 : 4); ++c) {
+            const int sx = (c & 1) ? hi[0] : lo[0], sy = (c & 2) ? hi[1] : lo[1], sz = (c & 4) ? hi[2] : lo[2];
+            const double w = ((c & 1) ? w1[0] : 1.0 - w1[0]) * ((c & 2) ? w1[1] : 1.0 - w1[1]) *
+                             (D == 3 ? ((c & 4) ? w1[2] : 1.0 - w1[2]) : 1.0);
+            const unsigned idx = ((unsigned)sz * (unsigned)g.ny + (unsigned)sy) * (unsigned)g.nx + (unsigned)sx;
+            double rho, u[3];
+            site_moments<L, S, WALLS>(f.m, idx, rho, u);
+            acc[0] += w * (rho - 1.0);
+            for (int k = 0; k < 3; ++k) acc[1 + k] += w * u[k];
+        }
+        float* o = f.out + ((size_t)p * nn + q) * 4;
+        o[0] = (float)(acc[0] / f.u_ref);
+        for (int k = 0; k < 3; ++k) o[1 + k] = (float)((acc[1 + k] - f.pk[p].u[k]) / f.u_ref);
+    }
 }
 
 template <class L, typename S>
@@ -878,6 +938,20 @@ void launch_materialize(const MaterializeArgs& a, cudaStream_t s)
 }
 
 template <typename S>
+void launch_features(const FeatureArgs& f, cudaStream_t s)
+{
+    if (f.np == 0) return;
+    const bool walls = f.m.g.wall[0] || f.m.g.wall[1] || f.m.g.wall[2];
+    if (f.m.lattice == 0) {
+        if (walls) k_features<D2Q9, S, true><<<f.np, 64, 0, s>>>(f);
+        else k_features<D2Q9, S, false><<<f.np, 64, 0, s>>>(f);
+    } else {
+        if (walls) k_features<D3Q19, S, true><<<f.np, 64, 0, s>>>(f);
+        else k_features<D3Q19, S, false><<<f.np, 64, 0, s>>>(f);
+    }
+}
+
+template <typename S>
 void launch_convert_in(const ConvertArgs& a, cudaStream_t s)
 {
     const unsigned blocks = (a.count + 255) / 256;
@@ -969,6 +1043,7 @@ const KernelTable* make_table()
                                   launch_sweep_batch<S>,
                                   launch_stash_fix_batch<S>,
                                   launch_update_masks_batch<S>,
+                                  launch_features<S>,
                                   (int)sizeof(S),
                                   (int)sizeof(typename Store<S>::C)};
     return &t;

@@ -29,10 +29,14 @@ EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_par
             "lbm_last_error", "lbm_destroy",
             "lbm_batch_create", "lbm_batch_add_particles", "lbm_batch_cell", "lbm_batch_set_tuning",
             "lbm_batch_step", "lbm_batch_synchronize", "lbm_batch_profile_steps", "lbm_batch_get_info",
-            "lbm_batch_stream", "lbm_schedule_tiles", "lbm_batch_last_error", "lbm_batch_destroy")
+            "lbm_batch_stream", "lbm_schedule_tiles", "lbm_batch_last_error", "lbm_batch_destroy",
+            "lbm_closure_features",
+            "lbm_mlp_create", "lbm_mlp_num_params", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_forward",
+            "lbm_mlp_loss_grad", "lbm_mlp_adam_step", "lbm_mlp_train", "lbm_mlp_last_error", "lbm_mlp_destroy")
 # entry points whose return value is not an lbm_status
 _NOT_STATUS = ("lbm_last_error", "lbm_destroy", "lbm_batch_cell", "lbm_batch_stream", "lbm_schedule_tiles",
-               "lbm_batch_last_error", "lbm_batch_destroy")
+               "lbm_batch_last_error", "lbm_batch_destroy", "lbm_mlp_num_params", "lbm_mlp_last_error",
+               "lbm_mlp_destroy")
 
 
 class LbmError(RuntimeError):
@@ -90,6 +94,20 @@ def load(path: str = LIB_PATH):
     lib.lbm_batch_last_error.restype = ctypes.c_char_p
     lib.lbm_batch_destroy.argtypes = [P]
     lib.lbm_batch_destroy.restype = None
+    lib.lbm_closure_features.argtypes = [P, i32, ctypes.c_double, ctypes.c_double, P]
+    lib.lbm_mlp_create.argtypes = [ctypes.POINTER(P), i32, I, P]
+    lib.lbm_mlp_num_params.argtypes = [P]
+    lib.lbm_mlp_num_params.restype = ctypes.c_longlong
+    lib.lbm_mlp_set_params.argtypes = [P, D]
+    lib.lbm_mlp_get_params.argtypes = [P, D, D]
+    lib.lbm_mlp_forward.argtypes = [P, P, i32, P]
+    lib.lbm_mlp_loss_grad.argtypes = [P, P, P, i32, D]
+    lib.lbm_mlp_adam_step.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.lbm_mlp_train.argtypes = [P, P, P, i32, i32, i32, ctypes.c_double, ctypes.c_uint, D]
+    lib.lbm_mlp_last_error.argtypes = [P]
+    lib.lbm_mlp_last_error.restype = ctypes.c_char_p
+    lib.lbm_mlp_destroy.argtypes = [P]
+    lib.lbm_mlp_destroy.restype = None
     for name in EXPORTED:
         if name not in _NOT_STATUS:
             getattr(lib, name).restype = ctypes.c_int
@@ -413,6 +431,14 @@ class Simulation:
     def profile(self, n):
         return lbm_profile_steps(self.h, n)
 
+    def closure_features(self, n_side, spacing, u_ref):
+        """Closure inputs of every particle as a CUDA float32 tensor [np, n_side^3 * 4]."""
+        import torch
+        out = torch.empty((self.np, n_side ** 3 * 4), dtype=torch.float32, device="cuda")
+        lbm_closure_features(self.h, n_side, spacing, u_ref, out.data_ptr())
+        self.synchronize()
+        return out
+
 
 class Batch:
     """An ensemble of independent cells stepped together (lbm_batch_*)."""
@@ -464,3 +490,139 @@ class Batch:
     @property
     def stream(self):
         return lbm_batch_stream(self.h)
+
+
+def lbm_closure_features(h, n_side, spacing, u_ref, out_ptr):
+    _check(h, load().lbm_closure_features(h, int(n_side), float(spacing), float(u_ref), ctypes.c_void_p(out_ptr)))
+
+
+def _mcheck(h, status):
+    if status != LBM_OK:
+        msg = load().lbm_mlp_last_error(h) if h else b"(no network)"
+        raise LbmError(status, msg.decode(errors="replace") if msg else "")
+
+
+def lbm_mlp_create(sizes, cuda_stream=None):
+    sz = np.ascontiguousarray(sizes, dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = load().lbm_mlp_create(ctypes.byref(h), len(sz) - 1, _ip(sz), ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_mlp_create(%s)" % list(sizes))
+    return h
+
+
+def lbm_mlp_num_params(h):
+    return int(load().lbm_mlp_num_params(h))
+
+
+def lbm_mlp_set_params(h, flat):
+    flat = _f64(flat)
+    _mcheck(h, load().lbm_mlp_set_params(h, _dp(flat)))
+
+
+def lbm_mlp_get_params(h, params=True, grads=False):
+    n = lbm_mlp_num_params(h)
+    p = np.empty(n) if params else None
+    g = np.empty(n) if grads else None
+    _mcheck(h, load().lbm_mlp_get_params(h, _dp(p), _dp(g)))
+    return p, g
+
+
+def lbm_mlp_forward(h, x_ptr, rows, y_ptr):
+    _mcheck(h, load().lbm_mlp_forward(h, ctypes.c_void_p(x_ptr), int(rows), ctypes.c_void_p(y_ptr)))
+
+
+def lbm_mlp_loss_grad(h, x_ptr, t_ptr, rows, want_loss=True):
+    loss = ctypes.c_double(0.0)
+    _mcheck(h, load().lbm_mlp_loss_grad(h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(rows),
+                                        ctypes.byref(loss) if want_loss else None))
+    return loss.value
+
+
+def lbm_mlp_adam_step(h, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _mcheck(h, load().lbm_mlp_adam_step(h, float(lr), float(beta1), float(beta2), float(eps)))
+
+
+def lbm_mlp_train(h, x_ptr, t_ptr, n, batch, epochs, lr, seed=0):
+    out = np.zeros(epochs)
+    _mcheck(h, load().lbm_mlp_train(h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(n), int(batch), int(epochs),
+                                    float(lr), int(seed), _dp(out)))
+    return out
+
+
+def lbm_mlp_last_error(h):
+    m = load().lbm_mlp_last_error(h)
+    return m.decode(errors="replace") if m else ""
+
+
+def lbm_mlp_destroy(h):
+    if h:
+        load().lbm_mlp_destroy(h)
+
+
+def pack_params(layers):
+    """[[W, b], ...] (W: out x in) -> the flat layer-major vector of the C-ABI."""
+    return np.concatenate([np.concatenate([np.ravel(W), np.ravel(b)]) for W, b in layers])
+
+
+def unpack_params(flat, sizes):
+    out, o = [], 0
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        W = np.asarray(flat[o:o + a * b]).reshape(b, a)
+        o += a * b
+        out.append([W, np.asarray(flat[o:o + b])])
+        o += b
+    return out
+
+
+class MLP:
+    """The closure network on the GPU. Data arguments are torch CUDA tensors (FP32,
+    contiguous, row-major); torch only provides their memory."""
+
+    def __init__(self, sizes, cuda_stream=None):
+        self.sizes = list(sizes)
+        self.h = lbm_mlp_create(sizes, cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_params(self, layers):
+        lbm_mlp_set_params(self.h, pack_params(layers))
+
+    def params(self):
+        p, _ = lbm_mlp_get_params(self.h)
+        return unpack_params(p, self.sizes)
+
+    def grads(self):
+        _, g = lbm_mlp_get_params(self.h, params=False, grads=True)
+        return unpack_params(g, self.sizes)
+
+    @staticmethod
+    def _check(t, cols):
+        if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32" and t.dim() == 2 and t.shape[1] == cols):
+            raise ValueError("expected a contiguous CUDA float32 tensor with %d columns" % cols)
+
+    def forward(self, x):
+        import torch
+        self._check(x, self.sizes[0])
+        y = torch.empty((x.shape[0], self.sizes[-1]), dtype=torch.float32, device=x.device)
+        lbm_mlp_forward(self.h, x.data_ptr(), x.shape[0], y.data_ptr())
+        return y
+
+    def loss_grad(self, x, t):
+        self._check(x, self.sizes[0])
+        self._check(t, self.sizes[-1])
+        return lbm_mlp_loss_grad(self.h, x.data_ptr(), t.data_ptr(), x.shape[0])
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        lbm_mlp_adam_step(self.h, lr, beta1, beta2, eps)
+
+    def train(self, x, t, batch, epochs, lr, seed=0):
+        self._check(x, self.sizes[0])
+        self._check(t, self.sizes[-1])
+        return lbm_mlp_train(self.h, x.data_ptr(), t.data_ptr(), x.shape[0], batch, epochs, lr, seed)

@@ -92,3 +92,25 @@ def test_bf16_emulation_stays_close_to_fp64():
     assert abs(l16 - l64) <= 2e-2 * l64
     for a, b in zip(g64, g16):
         assert np.max(np.abs(a[0] - b[0])) <= 0.15 * np.max(np.abs(a[0]))
+
+
+def test_stencil_features_interpolate_linear_fields_exactly():
+    # trilinear interpolation reproduces a linear field; nodes are kept away from the wrap
+    nz, ny, nx = 20, 22, 24
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    rho = 1.0 + 1e-3 * (0.5 * x - 0.25 * y + 0.125 * z)
+    u = np.stack([2e-3 * x + 1e-4, -1e-3 * y, 5e-4 * (x + z)], axis=-1)
+    centers = np.array([[11.3, 10.7, 9.2], [12.05, 11.5, 10.0]])
+    up = np.array([[1e-4, 0.0, -2e-4], [0.0, 0.0, 0.0]])
+    n, h, U = 4, 1.7, 2e-3
+    F = M.stencil_features(rho, u, centers, up, n, h, U)
+    for p in range(2):
+        for k in range(n):
+            for j in range(n):
+                for i in range(n):
+                    X = centers[p] + h * (np.array([i, j, k]) - 1.5)
+                    q = (k * n + j) * n + i
+                    want = [1e-3 * (0.5 * X[0] - 0.25 * X[1] + 0.125 * X[2]) / U,
+                            (2e-3 * X[0] + 1e-4 - up[p, 0]) / U, (-1e-3 * X[1] - up[p, 1]) / U,
+                            (5e-4 * (X[0] + X[2]) - up[p, 2]) / U]
+                    assert np.allclose(F[p, 4 * q:4 * q + 4], want, rtol=0, atol=1e-12)
