@@ -52,11 +52,13 @@ lbm_status ensure_alloc(lbm_ctx* ctx)
     CS(dev_alloc(ctx, &ctx->f[1], fbytes));
     CS(dev_alloc(ctx, &ctx->status, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->pending, sizeof(int)));
+    CS(dev_alloc(ctx, &ctx->pending_prev, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->step_id, sizeof(unsigned)));
     CS(dev_alloc(ctx, &ctx->wv, 2 * sizeof(WallVel)));
     CS(dev_alloc(ctx, &ctx->staging, STAGING_BYTES));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(ctx->pending, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(ctx->pending_prev, 0, sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(ctx->step_id, 0, sizeof(unsigned), ctx->stream));
     {
         const WallVel w[2] = {wall_vel(ctx), wall_vel(ctx)};
@@ -142,6 +144,9 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     a.np = ctx->np;
     a.pk = ctx->pk;
     a.pkf = ctx->pkf;
+    a.pk_prev = ctx->pk_prev;
+    a.pkf_prev = ctx->pkf_prev;
+    a.pending_prev = ctx->pending_prev;
     a.pc = ctx->pc;
     a.tmpl = ctx->tmpl;
     a.tag = ctx->tag;
@@ -208,8 +213,6 @@ SweepArgs sweep_args(lbm_ctx* ctx, int c)
     a.fin = ctx->f[c];
     a.fout = ctx->f[1 - c];
     a.pv = part_view(ctx);
-    a.stash_in = ctx->stash[c];
-    a.stash_out = ctx->stash[1 - c];
     a.bs_scratch = ctx->bs_scratch;
     a.omega = 1.0 / ctx->tau;
     a.pre = 1.0 - 0.5 / ctx->tau;
@@ -221,17 +224,21 @@ SweepArgs sweep_args(lbm_ctx* ctx, int c)
     return a;
 }
 
-// Arguments of the IS-density fix-up after a step that wrote buffer 1 - c.
-StashFixArgs stash_fix_args(lbm_ctx* ctx, int c)
+// Arguments of the IS-site bookkeeping after the sweep that read buffer c and wrote 1 - c:
+// that sweep's arguments with the particle view it ran with (the copies taken at the start
+// of the particle phase).
+ISFixArgs is_fix_args(lbm_ctx* ctx, int c)
 {
-    StashFixArgs s{};
-    s.lattice = ctx->lattice;
-    s.g = ctx->g;
-    s.fout = ctx->f[1 - c];
-    s.stash_out = ctx->stash[1 - c];
+    ISFixArgs s{};
+    s.s = sweep_args(ctx, c);
+    s.s.pv.pk = ctx->pk_prev;
+    s.s.pv.pkf = ctx->pkf_prev;
+    s.s.pv.pending = ctx->pending_prev;
+    s.dens = ctx->dens;
     s.pk = ctx->pk;
     s.pc = ctx->pc;
     s.tmpl = ctx->tmpl;
+    s.Kold = ctx->Kold;
     s.list = ctx->changed;
     s.cnt = ctx->cnt;
     return s;
@@ -247,10 +254,14 @@ int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
     if (ev) cudaEventRecord(ev[1], ctx->stream);
     int launches = 1;
     if (ctx->np > 0) {
-        launches += launch_particle_phase(particle_args(ctx), ctx->stream);
-        ctx->kt->stash_fix(stash_fix_args(ctx, c), ctx->stream);
+        const ParticleArgs pa = particle_args(ctx);
+        const ISFixArgs fa = is_fix_args(ctx, c);
+        launches += launch_particle_phase_a(pa, ctx->stream);
+        ctx->kt->is_save(fa, ctx->stream);
+        launches += launch_particle_phase_b(pa, ctx->stream);
+        ctx->kt->is_fix(fa, ctx->stream);
         ctx->kt->update_masks(mask_args(ctx, true), ctx->stream);
-        launches += 2;
+        launches += 4;
     }
     if (ctx->moving_walls) {
         launch_wall_advance(ctx->wv, ctx->pending, ctx->stream);
@@ -572,7 +583,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
         if (it != ctx->allocs.end()) ctx->allocs.erase(it);
         cudaFree(p);
     };
-    for (void* p : {(void*)ctx->pk, (void*)ctx->pkf, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->un,
+    for (void* p : {(void*)ctx->pk, (void*)ctx->pkf, (void*)ctx->pk_prev, (void*)ctx->pkf_prev, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->un,
                     (void*)ctx->acc, (void*)ctx->force, (void*)ctx->Kold, (void*)ctx->cell_of,
                     (void*)ctx->cell_count, (void*)ctx->cell_start, (void*)ctx->cell_cursor,
                     (void*)ctx->cell_items, (void*)ctx->changed, (void*)ctx->restamp,
@@ -581,6 +592,8 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     const size_t np = (size_t)ctx->np;
     CS(dev_alloc(ctx, &ctx->pk, sizeof(PKern) * np));
     CS(dev_alloc(ctx, &ctx->pkf, sizeof(PKernF) * np));
+    CS(dev_alloc(ctx, &ctx->pk_prev, sizeof(PKern) * np));
+    CS(dev_alloc(ctx, &ctx->pkf_prev, sizeof(PKernF) * np));
     CS(dev_alloc(ctx, &ctx->pc, sizeof(PConst) * np));
     CS(dev_alloc(ctx, &ctx->tmpl, sizeof(int) * ctx->h_tmpl.size()));
     CS(dev_alloc(ctx, &ctx->x, sizeof(double) * 3 * np));
@@ -596,8 +609,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CS(dev_alloc(ctx, &ctx->pout, sizeof(double) * 15 * np));
     if (!ctx->tag) {
         CS(dev_alloc(ctx, &ctx->tag, sizeof(unsigned) * (size_t)ctx->g.N));
-        CS(dev_alloc(ctx, &ctx->stash[0], (size_t)ctx->kt->compute_bytes * ctx->g.N));
-        CS(dev_alloc(ctx, &ctx->stash[1], (size_t)ctx->kt->compute_bytes * ctx->g.N));
+        CS(dev_alloc(ctx, &ctx->dens, (size_t)ctx->kt->compute_bytes * ctx->g.N));
         CS(dev_alloc(ctx, &ctx->cnt, sizeof(Counters)));
         CS(dev_alloc(ctx, &ctx->pairs, sizeof(unsigned long long) * PAIR_CAP));
         CS(dev_alloc(ctx, &ctx->ismask, sizeof(unsigned) * (size_t)ctx->g.N));
@@ -711,7 +723,6 @@ static lbm_status materialize(lbm_ctx* ctx, int mode, double* out_a, double* out
         a.g = ctx->g;
         a.fin = ctx->f[ctx->cur];
         a.pv = part_view(ctx);
-        a.stash_in = ctx->stash[ctx->cur];
         for (int k = 0; k < 3; ++k) a.F[k] = ctx->F[k];
         wall_args(ctx, a);
         a.s0 = (unsigned)s0;
@@ -747,7 +758,6 @@ lbm_status lbm_closure_features(lbm_ctx* ctx, int n_side, double spacing, double
     f.m.g = ctx->g;
     f.m.fin = ctx->f[ctx->cur];
     f.m.pv = part_view(ctx);
-    f.m.stash_in = ctx->stash[ctx->cur];
     for (int k = 0; k < 3; ++k) f.m.F[k] = ctx->F[k];
     wall_args(ctx, f.m);
     f.x = ctx->x;

@@ -30,7 +30,7 @@ struct lbm_batch {
 
     // device-side argument arrays and schedule
     SweepArgs* d_sweep[2] = {nullptr, nullptr};
-    StashFixArgs* d_stash[2] = {nullptr, nullptr};
+    ISFixArgs* d_isfix[2] = {nullptr, nullptr};
     ParticleArgs* d_part = nullptr;
     MaskArgs* d_mask = nullptr;
     int4* d_table = nullptr;
@@ -91,7 +91,7 @@ void release_device(lbm_batch* b)
     for (void* p : b->allocs) cudaFree(p);
     b->allocs.clear();
     b->d_sweep[0] = b->d_sweep[1] = nullptr;
-    b->d_stash[0] = b->d_stash[1] = nullptr;
+    b->d_isfix[0] = b->d_isfix[1] = nullptr;
     b->d_part = nullptr;
     b->d_mask = nullptr;
     b->d_table = nullptr;
@@ -127,10 +127,13 @@ int enqueue_batch_step(lbm_batch* b, int c, cudaEvent_t* ev = nullptr)
     if (ev) cudaEventRecord(ev[1], b->stream);
     int launches = 1;
     if (b->any_part) {
-        launches += launch_particle_phase_batch(b->d_part, b->shape, b->stream);
-        b->kt->stash_fix_batch(b->lattice, b->d_stash[c], (int)b->cells.size(), b->stream);
-        b->kt->update_masks_batch(b->lattice, b->d_mask, (int)b->cells.size(), b->stream);
-        launches += 2;
+        const int nc = (int)b->cells.size();
+        launches += launch_particle_phase_batch_a(b->d_part, b->shape, b->stream);
+        b->kt->is_save_batch(b->lattice, b->d_isfix[c], nc, b->stream);
+        launches += launch_particle_phase_batch_b(b->d_part, b->shape, b->stream);
+        b->kt->is_fix_batch(b->lattice, b->d_isfix[c], nc, b->stream);
+        b->kt->update_masks_batch(b->lattice, b->d_mask, nc, b->stream);
+        launches += 4;
     }
     for (int i : b->moving) {
         launch_wall_advance(b->cells[(size_t)i]->wv, b->cells[(size_t)i]->pending, b->stream);
@@ -193,14 +196,14 @@ lbm_status build(lbm_batch* b)
     for (lbm_ctx* ctx : b->cells) b->built_np.push_back(ctx->np);
 
     std::vector<SweepArgs> sw[2];
-    std::vector<StashFixArgs> st[2];
+    std::vector<ISFixArgs> st[2];
     std::vector<ParticleArgs> pa;
     std::vector<MaskArgs> ma;
     for (int i = 0; i < nc; ++i) {
         lbm_ctx* ctx = b->cells[(size_t)i];
         for (int c = 0; c < 2; ++c) {
             sw[c].push_back(sweep_args(ctx, c));
-            st[c].push_back(ctx->np > 0 ? stash_fix_args(ctx, c) : StashFixArgs{});
+            st[c].push_back(ctx->np > 0 ? is_fix_args(ctx, c) : ISFixArgs{});
         }
         if (ctx->np > 0) {
             ParticleArgs p = particle_args(ctx);
@@ -226,7 +229,7 @@ lbm_status build(lbm_batch* b)
     b->ntiles = (int)nt;
     for (int c = 0; c < 2; ++c) {
         BS(upload(b, &b->d_sweep[c], sw[c]));
-        BS(upload(b, &b->d_stash[c], st[c]));
+        BS(upload(b, &b->d_isfix[c], st[c]));
     }
     BS(upload(b, &b->d_part, pa));
     BS(upload(b, &b->d_mask, ma));

@@ -38,7 +38,7 @@ struct lbm_ctx {
     bool stepped = false;
 
     void* f[2] = {nullptr, nullptr};
-    void* stash[2] = {nullptr, nullptr};
+    void* dens = nullptr;      // [N] compute type: site densities for the IS bookkeeping
     unsigned* tag = nullptr;
     unsigned* ismask = nullptr;
     void* bs_scratch = nullptr;
@@ -52,6 +52,8 @@ struct lbm_ctx {
     std::vector<int> h_tmpl;
     lbmp::PKern* pk = nullptr;
     lbmp::PKernF* pkf = nullptr;
+    lbmp::PKern* pk_prev = nullptr;
+    lbmp::PKernF* pkf_prev = nullptr;
     lbmp::PConst* pc = nullptr;
     int* tmpl = nullptr;
     double *x = nullptr, *un = nullptr, *acc = nullptr, *force = nullptr;
@@ -59,6 +61,7 @@ struct lbm_ctx {
     lbmp::Counters* cnt = nullptr;
     int* status = nullptr;
     int* pending = nullptr;
+    int* pending_prev = nullptr;
     unsigned* step_id = nullptr;
     lbmp::CellGrid cg{};
     int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_cursor = nullptr,
@@ -134,7 +137,7 @@ ParticleArgs particle_args(lbm_ctx* ctx);
 MaskArgs mask_args(lbm_ctx* ctx, bool restamp_list);
 PartView part_view(lbm_ctx* ctx);
 SweepArgs sweep_args(lbm_ctx* ctx, int c);
-StashFixArgs stash_fix_args(lbm_ctx* ctx, int c);
+ISFixArgs is_fix_args(lbm_ctx* ctx, int c);
 
 }  // namespace host
 }  // namespace lbmp

@@ -16,8 +16,6 @@ struct SweepArgs {
     const void* fin;           // [Q][N] storage format
     void* fout;                // [Q][N]
     PartView pv;               // tag == nullptr: no particles
-    const void* stash_in;      // [N] compute type (double / float): site density (deviation)
-    void* stash_out;           // [N]
     void* bs_scratch;          // per-site dP, dL at BS sites: FP64 mode [N][6] doubles; FP32 modes
                                // [N][8] floats (dP, dL, owner tag bits, step id bits: one 32-byte
                                // sector)
@@ -32,7 +30,6 @@ struct MaterializeArgs {
     Geom g;
     const void* fin;
     PartView pv;
-    const void* stash_in;
     double F[3];
     int moving_walls;
     const WallVel* uw;
@@ -57,14 +54,19 @@ struct UnstreamArgs {
     void* dst;                 // [Q][N] pull-source layout
 };
 
-struct StashFixArgs {
-    int lattice;
-    Geom g;
-    const void* fout;          // [Q][N] buffer just written by the sweep
-    void* stash_out;           // [N]
-    const PKern* pk;
+// The IS-site bookkeeping of one step (see k_is_density, k_is_restore, k_is_fix). Every
+// site tagged IS when a sweep runs stores its post-collision density (in the compute form:
+// rho, or rho - 1 for deviation storage) in all Q of its slots instead of its populations,
+// which no pull ever uses raw (every pull from an IS site takes the imposed equilibrium).
+// When a particle's shift changes, the sites that stop being IS get their populations back
+// and the sites that become IS get their density.
+struct ISFixArgs {
+    SweepArgs s;               // the step's sweep, with the particle view it ran with (prev copies)
+    void* dens;                // [N] compute type: densities of the sites visited
+    const PKern* pk;           // current particle records (new anchors)
     const PConst* pc;
     const int* tmpl;
+    const int* Kold;           // [np][3] anchors the sweep ran with
     const int* list;           // particles whose shift changed
     const Counters* cnt;       // cnt->nchanged entries of list
 };
@@ -97,7 +99,7 @@ struct BatchSweepArgs {
 
 // Inputs of the closure network: stencil moments around each particle (see k_features).
 struct FeatureArgs {
-    MaterializeArgs m;         // the state (buffer, particle view, stash, walls, F)
+    MaterializeArgs m;         // the state (buffer, particle view, walls, F)
     const double* x;           // [np][3] centres
     const PKern* pk;           // particle velocities
     int np;
@@ -114,10 +116,12 @@ struct KernelTable {
     void (*convert_in)(const ConvertArgs&, cudaStream_t);
     void (*unstream)(const UnstreamArgs&, cudaStream_t);
     void (*fill_rest)(int lattice, void* dst, unsigned N, cudaStream_t);
-    void (*stash_fix)(const StashFixArgs&, cudaStream_t);
+    void (*is_save)(const ISFixArgs&, cudaStream_t);   // densities, then populations restored
+    void (*is_fix)(const ISFixArgs&, cudaStream_t);    // densities into the new IS sites
     void (*sweep_batch)(const BatchSweepArgs&, cudaStream_t);
     // per-cell argument arrays on the device, blockIdx.y = cell
-    void (*stash_fix_batch)(int lattice, const StashFixArgs* cells, int ncells, cudaStream_t);
+    void (*is_save_batch)(int lattice, const ISFixArgs* cells, int ncells, cudaStream_t);
+    void (*is_fix_batch)(int lattice, const ISFixArgs* cells, int ncells, cudaStream_t);
     void (*update_masks_batch)(int lattice, const MaskArgs* cells, int ncells, cudaStream_t);
     void (*features)(const FeatureArgs&, cudaStream_t);
     int elem_bytes;
@@ -142,6 +146,9 @@ struct ParticleArgs {
     int np;
     PKern* pk;
     PKernF* pkf;        // FP32 copy of pk, refreshed after the move
+    PKern* pk_prev;     // [np] pk, pkf and *pending as the step's sweep saw them (copied
+    PKernF* pkf_prev;   // at the start of the particle phase)
+    int* pending_prev;
     const PConst* pc;
     const int* tmpl;
     unsigned* tag;
@@ -170,9 +177,12 @@ struct ParticleArgs {
     double gap;
 };
 
-// Enqueues the particle phase of one step after the sweep: reduction (FP64 mode),
-// acceleration, contacts, move, re-marking. Returns the number of kernels launched.
-int launch_particle_phase(const ParticleArgs& a, cudaStream_t s);
+// Enqueues the particle phase of one step after the sweep in two parts: (a) snapshot of the
+// sweep's particle view, reduction, acceleration, contacts, move, the list of particles to
+// re-mark; (b) re-marking of the owner map. The IS-site bookkeeping (ISFixArgs) runs between
+// them, while the owner map is still the one the sweep used. Return the kernels launched.
+int launch_particle_phase_a(const ParticleArgs& a, cudaStream_t s);
+int launch_particle_phase_b(const ParticleArgs& a, cudaStream_t s);
 // Stamps every particle's site set into a cleared owner map (after lbm_add_particles).
 void launch_stamp_all(const ParticleArgs& a, cudaStream_t s);
 
@@ -185,7 +195,8 @@ struct PhaseShape {
     int pair_cap;     // contact-pair capacity of every cell (its resolve buffer)
     int scratch_f64;  // FP64 storage: ordered per-particle sums
 };
-int launch_particle_phase_batch(const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s);
+int launch_particle_phase_batch_a(const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s);
+int launch_particle_phase_batch_b(const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s);
 // After a sweep with moving walls: the current wall velocities become those of the streaming
 // that the next pull completes (wv[0] <- wv[1]), and the pulled values await streaming.
 void launch_wall_advance(WallVel* wv, int* pending, cudaStream_t s);

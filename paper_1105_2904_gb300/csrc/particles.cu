@@ -42,7 +42,12 @@ __global__ void k_phase_clear(const ParticleArgs a0, const ParticleArgs* __restr
         a.cell_count[i] = 0;
         a.cell_cursor[i] = 0;
     }
-    for (int i = t0; i < a.np; i += T) a.restamp_flag[i] = 0;
+    for (int i = t0; i < a.np; i += T) {
+        a.restamp_flag[i] = 0;
+        a.pk_prev[i] = a.pk[i];
+        a.pkf_prev[i] = a.pkf[i];
+    }
+    if (t0 == 0) *a.pending_prev = *a.pending;
 }
 
 // d - n floor(d/n + 1/2). For |d| < n/4, d/n + 1/2 lies in (1/4, 3/4) whatever the
@@ -535,11 +540,10 @@ __global__ void k_pack_particles(const ParticleArgs a, double* out)
 }
 
 template <bool B>
-int particle_phase(const ParticleArgs& a0, const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s)
+int particle_phase_a(const ParticleArgs& a0, const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s)
 {
     const int nc = sh.ncells;
     const dim3 gp((sh.max_np + PT - 1) / PT, nc);
-    const int per_cell = std::max(2, mark_grid() / nc);
     k_phase_clear<B><<<dim3(std::max(1, std::min(64, (std::max(sh.max_np, sh.max_cells) + 255) / 256)), nc), 256, 0, s>>>(
         a0, cells);
     if (sh.scratch_f64)
@@ -555,14 +559,20 @@ int particle_phase(const ParticleArgs& a0, const ParticleArgs* cells, const Phas
     k_resolve<B><<<dim3(1, nc), rthreads, smem, s>>>(a0, cells);
     k_move<B><<<gp, PT, 0, s>>>(a0, cells);
     k_mark_neighbours<B><<<gp, PT, 0, s>>>(a0, cells);
-    k_mark_clear<B><<<dim3(per_cell, nc), 256, 0, s>>>(a0, cells);
-    k_mark_stamp<B><<<dim3(per_cell, nc), 256, 0, s>>>(a0, cells);
-    return 12;
+    return 10;
 }
 
-}  // namespace
+template <bool B>
+int particle_phase_b(const ParticleArgs& a0, const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s)
+{
+    const int nc = sh.ncells;
+    const int per_cell = std::max(2, mark_grid() / nc);
+    k_mark_clear<B><<<dim3(per_cell, nc), 256, 0, s>>>(a0, cells);
+    k_mark_stamp<B><<<dim3(per_cell, nc), 256, 0, s>>>(a0, cells);
+    return 2;
+}
 
-int launch_particle_phase(const ParticleArgs& a, cudaStream_t s)
+PhaseShape single_shape(const ParticleArgs& a)
 {
     PhaseShape sh{};
     sh.ncells = 1;
@@ -570,12 +580,29 @@ int launch_particle_phase(const ParticleArgs& a, cudaStream_t s)
     sh.max_cells = a.cg.total;
     sh.pair_cap = a.pair_cap;
     sh.scratch_f64 = a.scratch_f64;
-    return particle_phase<false>(a, nullptr, sh, s);
+    return sh;
 }
 
-int launch_particle_phase_batch(const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s)
+}  // namespace
+
+int launch_particle_phase_a(const ParticleArgs& a, cudaStream_t s)
 {
-    return particle_phase<true>(ParticleArgs{}, cells, sh, s);
+    return particle_phase_a<false>(a, nullptr, single_shape(a), s);
+}
+
+int launch_particle_phase_b(const ParticleArgs& a, cudaStream_t s)
+{
+    return particle_phase_b<false>(a, nullptr, single_shape(a), s);
+}
+
+int launch_particle_phase_batch_a(const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s)
+{
+    return particle_phase_a<true>(ParticleArgs{}, cells, sh, s);
+}
+
+int launch_particle_phase_batch_b(const ParticleArgs* cells, const PhaseShape& sh, cudaStream_t s)
+{
+    return particle_phase_b<true>(ParticleArgs{}, cells, sh, s);
 }
 
 void launch_pack_particles(const ParticleArgs& a, double* out, cudaStream_t s)

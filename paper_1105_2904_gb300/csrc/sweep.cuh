@@ -8,9 +8,15 @@
 // The IS imposition of the previous step (Eq. 12, "velocity of the internal sites") is
 // applied as populations are pulled: a value pulled from a site tagged IS of particle p is
 // replaced by f^eq_d(rho_I, u_p + omega_p x r), with rho_I the post-collision density of
-// that site, saved by the previous sweep (the "stash"). Only sites inside a particle can
-// pull from an IS site (every neighbour of an IS site lies in the particle), so fluid sites
-// never look. This removes a separate scattered pass over the IS shell.
+// that site. Only sites inside a particle can pull from an IS site (every neighbour of an IS
+// site lies in the particle), so fluid sites never look. This removes a separate scattered
+// pass over the IS shell.
+//
+// Density carry: since no pull uses the populations of an IS site raw, the sweep stores an
+// IS site's post-collision density rho_I in all Q of its slots instead. The value a site
+// pulls from an IS source is then rho_I itself: the imposition needs no second, dependent
+// load. The particle phase keeps this true when site sets move (k_is_density, k_is_restore,
+// k_is_fix).
 #pragma once
 
 #include <type_traits>
@@ -313,16 +319,15 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, const Geom& g, c
 
 // Applies the pending IS imposition (Eq. 12) to the values a site inside a particle pulls:
 // a value pulled from an IS site s in direction i becomes f^eq(rho_I(s), u_p + omega_p x r(s))
-// of the stored direction. `m` is the site's IS-source mask (bit i: the source of direction
-// i is an IS site of the site's own owner; MASK_OTHER: some source belongs to another
-// particle).
+// of the stored direction, where the pulled value itself is rho_I(s) (density carry). `m` is
+// the site's IS-source mask (bit i: the source of direction i is an IS site of the site's
+// own owner; MASK_OTHER: some source belongs to another particle).
 //
 // FP64 form: every substituted value is recomputed from its own lever arm, exactly as a
 // direct implementation of Eq. 12 does.
 template <class L, bool WALLS>
 __device__ __forceinline__ void substitute_is_plain(const Geom& g, const Nbr& n, int x, int y, int z,
-                                                    unsigned idx, unsigned m, const PartView& pv,
-                                                    const double* __restrict__ stash, double f[])
+                                                    unsigned idx, unsigned m, const PartView& pv, double f[])
 {
     sfor<0, L::Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
@@ -337,27 +342,41 @@ __device__ __forceinline__ void substitute_is_plain(const Geom& g, const Nbr& n,
             double r[3], uI[3];
             lever_arm(g, k, sx, sy, sz, r);
             rigid_velocity(k, r, uI);
-            f[i] = feq_plain<L, i>(bounce ? -1.0 : 1.0, stash[sidx], uI);
+            f[i] = feq_plain<L, i>(bounce ? -1.0 : 1.0, f[i], uI);
         }
     });
+}
+
+// Whether the pull of direction i leaves the domain through a wall (then its source is the
+// site itself, stored direction opp(i)).
+template <class L, int i, bool WALLS>
+__device__ __forceinline__ bool pull_bounces(const Nbr& n)
+{
+    if constexpr (!WALLS) {
+        return false;
+    } else {
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        return (cx > 0 && n.bxm) || (cx < 0 && n.bxp) || (cy > 0 && n.bym) || (cy < 0 && n.byp) ||
+               (cz > 0 && n.bzm) || (cz < 0 && n.bzp);
+    }
 }
 
 // FP32 form. With u(s) = u(x) - omega x c_i for the source s = x - c_i of a rigid motion:
 // c_i.u(s) = c_i.u(x) (c_i.(omega x c_i) = 0) and
 // |u(s)|^2 = |u(x)|^2 - 2 c_i.(u(x) x omega) + |omega|^2 |c_i|^2 - (omega.c_i)^2,
-// so one rigid velocity per site serves all of its sources.
+// so one rigid velocity per site serves all of its sources. The work is warp-uniform: the
+// directions some lane of the warp needs are evaluated by every lane and kept where the
+// lane's own mask asks for them (no per-lane branches, no loads beyond the owner's record).
+// Every lane of the warp that is converged here calls it; m = 0 for sites with nothing to do.
 template <class L, bool WALLS>
 __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, int x, int y, int z,
-                                                  unsigned idx, unsigned m, unsigned owner,
-                                                  const PartView& pv, const float* __restrict__ stash,
-                                                  float f[])
+                                                  unsigned m, unsigned owner, const PartView& pv, float f[])
 {
     constexpr int Q = L::Q;
     const unsigned mm = m & ~MASK_OTHER;
-    if (mm) {
-        // directions no active lane of the warp needs are skipped as a whole
-        const unsigned wm = __reduce_or_sync(__activemask(), mm);
-        const PKernF k = pv.pkf[owner];
+    const unsigned wm = __reduce_or_sync(__activemask(), mm);
+    if (wm) {
+        const PKernF k = pv.pkf[mm ? owner : 0u];
         float r[3], ux[3];
         lever_arm(g, k, x, y, z, r);
         rigid_velocity(k, r, ux);
@@ -368,11 +387,9 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
         const float w2 = k.om[0] * k.om[0] + k.om[1] * k.om[1] + k.om[2] * k.om[2];
         // rest direction: only an IS site pulls its own rest population, f^eq_0 at u(x)
         if (wm & 1u) {
-            if (mm & 1u) {
-                const float E = -1.5f * usq;
-                const float drho = stash[idx];
-                f[0] = (float)L::w(0) * (E + drho * (1.0f + E));
-            }
+            const float E = -1.5f * usq;
+            const float val = (float)L::w(0) * (E + f[0] * (1.0f + E));
+            if (mm & 1u) f[0] = val;
         }
         // Opposite pair (i, j = opp(i)): with cu = c_i.u(x), ca = c_i.(u(x) x omega),
         // base = |u(x)|^2 + |omega|^2 |c_i|^2 - (c_i.omega)^2, the sources x - c_i and x - c_j
@@ -393,24 +410,16 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
                     const float base = usq + w2 * c2 - cw * cw;
                     const float S = 4.5f * cu * cu - 1.5f * base;
                     const float D = 3.0f * (cu + ca);
-                    if (mm & (1u << i)) {
-                        int sx, sy, sz;
-                        unsigned sidx;
-                        bool bounce;
-                        pull_source<L, i, WALLS>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
-                        const float E = bounce ? (4.5f * cu * cu - 1.5f * usq - 3.0f * cu) : S + D;
-                        const float drho = stash[sidx];
-                        f[i] = w * (E + drho * (1.0f + E));
+                    float Ei = S + D, Ej = S - D;
+                    if constexpr (WALLS) {
+                        const float Sb = 4.5f * cu * cu - 1.5f * usq;
+                        if (pull_bounces<L, i, WALLS>(n)) Ei = Sb - 3.0f * cu;
+                        if (pull_bounces<L, j, WALLS>(n)) Ej = Sb + 3.0f * cu;
                     }
-                    if (mm & (1u << j)) {
-                        int sx, sy, sz;
-                        unsigned sidx;
-                        bool bounce;
-                        pull_source<L, j, WALLS>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
-                        const float E = bounce ? (4.5f * cu * cu - 1.5f * usq + 3.0f * cu) : S - D;
-                        const float drho = stash[sidx];
-                        f[j] = w * (E + drho * (1.0f + E));
-                    }
+                    const float vi = w * (Ei + f[i] * (1.0f + Ei));
+                    const float vj = w * (Ej + f[j] * (1.0f + Ej));
+                    if (mm & (1u << i)) f[i] = vi;
+                    if (mm & (1u << j)) f[j] = vj;
                 }
             }
         });
@@ -438,10 +447,12 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
             const float sgn = bounce ? -1.0f : 1.0f;
             const float cu = sgn * ((float)cx * us[0] + (float)cy * us[1] + (float)cz * us[2]);
             const float usq = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
-            const float drho = stash[sidx];
-            const float val = w_rt<L>(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
             sfor<0, Q>([&](auto jc) {
-                if (i == decltype(jc)::value) f[decltype(jc)::value] = val;
+                constexpr int jj = decltype(jc)::value;
+                if (i == jj) {
+                    const float drho = f[jj];
+                    f[jj] = w_rt<L>(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+                }
             });
         }
     }
@@ -485,8 +496,11 @@ __global__ void k_update_masks(const MaskArgs a0, const MaskArgs* __restrict__ c
 }
 
 // Everything a site does after its populations are pulled: the pending IS imposition,
-// the collision, the BS transfer and its per-site record, the stores and the IS density.
-template <class L, typename S, bool WALLS, bool PART>
+// the collision, the BS transfer and its per-site record, and the stores (IS sites store
+// their density in every slot). RESTORE: store an IS site's populations instead (the
+// particle phase recomputing a site that stops being IS); the caller may be divergent.
+// Otherwise every lane of the warp calls it (tail lanes with valid = false).
+template <class L, typename S, bool WALLS, bool PART, bool RESTORE = false>
 __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int z, unsigned idx, bool valid,
                                            const Nbr& n, typename Store<S>::C f[], unsigned tagx, unsigned mask)
 {
@@ -495,15 +509,12 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
     constexpr int Q = L::Q;
     const Geom& g = a.g;
     if constexpr (PART) {
-        if (tagx != TAG_FLUID && *a.pv.pending) {
-            const unsigned m = mask;
-            if (m) {
-                if constexpr (St::deviation)
-                    substitute_is_dev<L, WALLS>(g, n, x, y, z, idx, m, tagx & PID_MASK, a.pv,
-                                                (const float*)a.stash_in, f);
-                else
-                    substitute_is_plain<L, WALLS>(g, n, x, y, z, idx, m, a.pv, (const double*)a.stash_in, f);
-            }
+        if (*a.pv.pending) {
+            const unsigned m = tagx != TAG_FLUID ? mask : 0u;
+            if constexpr (St::deviation)
+                substitute_is_dev<L, WALLS>(g, n, x, y, z, m, tagx & PID_MASK, a.pv, f);
+            else if (m)
+                substitute_is_plain<L, WALLS>(g, n, x, y, z, idx, m, a.pv, f);
         }
     }
     // A moving wall acts on the bounced value after the IS imposition it may have received.
@@ -598,20 +609,32 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
         }
     }
 
-    if (!valid) return;
     S* __restrict__ fout = (S*)a.fout;
     const size_t N = g.N;
-    // Post-collision density of IS sites, for the IS imposition pulled next step: the sum
-    // of the values as stored.
-    const bool isis = PART && (tagx >> 30) == CLS_IS;
-    C dens = (C)0;
-    sfor<0, Q>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        const S s = St::save(f[i], (C)L::w(i));
-        fout[(size_t)i * N + idx] = s;
-        if (isis) dens += St::load(s, (C)L::w(i));
-    });
-    if (isis) ((C*)a.stash_out)[idx] = dens;
+    // IS sites store their post-collision density, the sum of the values as stored, in
+    // every slot (density carry); the check is warp-uniform.
+    const bool isis = PART && !RESTORE && (tagx >> 30) == CLS_IS;
+    bool any_is = false;
+    if constexpr (PART && !RESTORE) any_is = __any_sync(__activemask(), isis);
+    if (!valid) return;
+    if (any_is) {
+        S s[Q];
+        C dens = (C)0;
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            s[i] = St::save(f[i], (C)L::w(i));
+            dens += St::load(s[i], (C)L::w(i));
+        });
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            fout[(size_t)i * N + idx] = isis ? St::save(dens, (C)L::w(i)) : s[i];
+        });
+    } else {
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            fout[(size_t)i * N + idx] = St::save(f[i], (C)L::w(i));
+        });
+    }
 }
 
 
@@ -688,10 +711,9 @@ __device__ __forceinline__ void site_pull(const MaterializeArgs& a, unsigned idx
         const unsigned m = a.pv.ismask[idx];
         if (m) {
             if constexpr (St::deviation)
-                substitute_is_dev<L, WALLS>(g, n, x, y, z, idx, m, a.pv.tag[idx] & PID_MASK, a.pv,
-                                            (const float*)a.stash_in, f);
+                substitute_is_dev<L, WALLS>(g, n, x, y, z, m, a.pv.tag[idx] & PID_MASK, a.pv, f);
             else
-                substitute_is_plain<L, WALLS>(g, n, x, y, z, idx, m, a.pv, (const double*)a.stash_in, f);
+                substitute_is_plain<L, WALLS>(g, n, x, y, z, idx, m, a.pv, f);
         }
     }
     if constexpr (WALLS) {
@@ -866,33 +888,114 @@ __global__ void k_fill_rest(S* dst, unsigned N)
     }
 }
 
-// Post-collision density at the new IS sites of particles whose shift changed (their IS
-// sites may not have been IS, hence not saved, during the sweep).
+// ---- IS-site bookkeeping when a particle's shift changes -------------------------------
+// Density carry keeps rho_I in every slot of the sites the sweep saw tagged IS. After the
+// move, the sites of a particle whose shift changed may stop or start being IS; these three
+// kernels (one block per such particle, threads over its IS template entries at the anchor
+// the sweep used and at the new one) restore the invariant for the new owner map.
+
+// Site of IS template entry e of particle p at anchor K (false if it leaves a walled domain).
+__device__ __forceinline__ bool is_entry_site(const ISFixArgs& a, const int K[3], int e, unsigned& site)
+{
+    int Kw[3];
+    wrap_anchor(a.s.g, K, Kw);
+    const int ent = a.tmpl[e];
+    return site_fast(a.s.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site);
+}
+
+// (1) Before the owner map changes: the density of every visited site, read from the
+// sweep's output (one slot of a site the sweep saw as IS, else the sum of its populations in
+// slot order, the sum the sweep takes).
 template <class L, typename S, bool B>
-__global__ void k_stash_fix(const StashFixArgs a0, const StashFixArgs* __restrict__ cells)
+__global__ void k_is_density(const ISFixArgs a0, const ISFixArgs* __restrict__ cells)
 {
     using St = Store<S>;
     using C = typename St::C;
-    const StashFixArgs a = pick_args<B>(a0, cells);
+    const ISFixArgs a = pick_args<B>(a0, cells);
     if (!a.cnt) return;
     const int nlist = a.cnt->nchanged;
-    const size_t N = a.g.N;
-    const S* fout = (const S*)a.fout;
-    C* stash = (C*)a.stash_out;
+    const size_t N = a.s.g.N;
+    const S* fo = (const S*)a.s.fout;
+    C* dens = (C*)a.dens;
     for (int b = blockIdx.x; b < nlist; b += gridDim.x) {
         const int p = a.list[b];
         const PConst pc = a.pc[p];
-        const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
-        for (int e = pc.n_bs + threadIdx.x; e < pc.n_bs + pc.n_is; e += blockDim.x) {
-            const int ent = a.tmpl[pc.tmpl_off + e];
+        const int Ko[3] = {a.Kold[(size_t)p * 3], a.Kold[(size_t)p * 3 + 1], a.Kold[(size_t)p * 3 + 2]};
+        const int Kn[3] = {a.pk[p].K[0], a.pk[p].K[1], a.pk[p].K[2]};
+        for (int e = threadIdx.x; e < 2 * pc.n_is; e += blockDim.x) {
             unsigned site;
-            if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
-            C s = (C)0;
+            if (!is_entry_site(a, e < pc.n_is ? Ko : Kn, pc.tmpl_off + pc.n_bs + e % pc.n_is, site)) continue;
+            C d = (C)0;
+            if ((a.s.pv.tag[site] >> 30) == CLS_IS) {
+                d = St::load(fo[site], (C)L::w(0));
+            } else {
+                sfor<0, L::Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    d += St::load(fo[(size_t)i * N + site], (C)L::w(i));
+                });
+            }
+            dens[site] = d;
+        }
+    }
+}
+
+// (2) Still before the owner map changes: the sites the sweep saw as IS of a particle whose
+// shift changed get the populations the sweep computed for them (recomputed from the
+// sweep's input with the sweep's particle view; same code, same result bit for bit).
+template <class L, typename S, bool WALLS, bool B>
+__global__ void k_is_restore(const ISFixArgs a0, const ISFixArgs* __restrict__ cells)
+{
+    using C = typename Store<S>::C;
+    const ISFixArgs a = pick_args<B>(a0, cells);
+    if (!a.cnt) return;
+    const int nlist = a.cnt->nchanged;
+    const Geom& g = a.s.g;
+    for (int b = blockIdx.x; b < nlist; b += gridDim.x) {
+        const int p = a.list[b];
+        const PConst pc = a.pc[p];
+        const int Ko[3] = {a.Kold[(size_t)p * 3], a.Kold[(size_t)p * 3 + 1], a.Kold[(size_t)p * 3 + 2]};
+        for (int e = threadIdx.x; e < pc.n_is; e += blockDim.x) {
+            unsigned site;
+            if (!is_entry_site(a, Ko, pc.tmpl_off + pc.n_bs + e, site)) continue;
+            const unsigned t = a.s.pv.tag[site];
+            if (t != ((CLS_IS << 30) | (unsigned)p)) continue;
+            const int x = (int)(site % (unsigned)g.nx);
+            const int y = (int)((site / (unsigned)g.nx) % (unsigned)g.ny);
+            const int z = (int)(site / ((unsigned)g.nx * (unsigned)g.ny));
+            const Nbr n = neighbours<WALLS>(g, x, y, z);
+            C f[L::Q];
+            pull<L, S, WALLS>((const S*)a.s.fin, g, n, x, y, z, site, f);
+            sweep_site<L, S, WALLS, true, true>(a.s, x, y, z, site, true, n, f, t, a.s.pv.ismask[site]);
+        }
+    }
+}
+
+// (3) After re-marking: every visited site that is now IS holds its density in every slot.
+template <class L, typename S, bool B>
+__global__ void k_is_fix(const ISFixArgs a0, const ISFixArgs* __restrict__ cells)
+{
+    using St = Store<S>;
+    using C = typename St::C;
+    const ISFixArgs a = pick_args<B>(a0, cells);
+    if (!a.cnt) return;
+    const int nlist = a.cnt->nchanged;
+    const size_t N = a.s.g.N;
+    S* fo = (S*)a.s.fout;
+    const C* dens = (const C*)a.dens;
+    for (int b = blockIdx.x; b < nlist; b += gridDim.x) {
+        const int p = a.list[b];
+        const PConst pc = a.pc[p];
+        const int Ko[3] = {a.Kold[(size_t)p * 3], a.Kold[(size_t)p * 3 + 1], a.Kold[(size_t)p * 3 + 2]};
+        const int Kn[3] = {a.pk[p].K[0], a.pk[p].K[1], a.pk[p].K[2]};
+        for (int e = threadIdx.x; e < 2 * pc.n_is; e += blockDim.x) {
+            unsigned site;
+            if (!is_entry_site(a, e < pc.n_is ? Ko : Kn, pc.tmpl_off + pc.n_bs + e % pc.n_is, site)) continue;
+            if ((a.s.pv.tag[site] >> 30) != CLS_IS) continue;
+            const C d = dens[site];
             sfor<0, L::Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                s += St::load(fout[(size_t)i * N + site], (C)L::w(i));
+                fo[(size_t)i * N + site] = St::save(d, (C)L::w(i));
             });
-            stash[site] = s;
         }
     }
 }
@@ -975,11 +1078,27 @@ void launch_fill_rest(int lattice, void* dst, unsigned N, cudaStream_t s)
     else k_fill_rest<D3Q19, S><<<blocks, 256, 0, s>>>((S*)dst, N);
 }
 
-template <typename S>
-void launch_stash_fix(const StashFixArgs& a, cudaStream_t s)
+template <class L, typename S, bool B>
+void launch_is_save_l(const ISFixArgs& a, const ISFixArgs* cells, dim3 grid, bool walls, cudaStream_t s)
 {
-    if (a.lattice == 0) k_stash_fix<D2Q9, S, false><<<256, 128, 0, s>>>(a, nullptr);
-    else k_stash_fix<D3Q19, S, false><<<256, 128, 0, s>>>(a, nullptr);
+    k_is_density<L, S, B><<<grid, 128, 0, s>>>(a, cells);
+    if (walls) k_is_restore<L, S, true, B><<<grid, 128, 0, s>>>(a, cells);
+    else k_is_restore<L, S, false, B><<<grid, 128, 0, s>>>(a, cells);
+}
+
+template <typename S>
+void launch_is_save(const ISFixArgs& a, cudaStream_t s)
+{
+    const bool walls = a.s.g.wall[0] || a.s.g.wall[1] || a.s.g.wall[2];
+    if (a.s.lattice == 0) launch_is_save_l<D2Q9, S, false>(a, nullptr, dim3(256), walls, s);
+    else launch_is_save_l<D3Q19, S, false>(a, nullptr, dim3(256), walls, s);
+}
+
+template <typename S>
+void launch_is_fix(const ISFixArgs& a, cudaStream_t s)
+{
+    if (a.s.lattice == 0) k_is_fix<D2Q9, S, false><<<256, 128, 0, s>>>(a, nullptr);
+    else k_is_fix<D3Q19, S, false><<<256, 128, 0, s>>>(a, nullptr);
 }
 
 template <typename S>
@@ -989,13 +1108,21 @@ void launch_update_masks(const MaskArgs& a, cudaStream_t s)
     else k_update_masks<D3Q19, false><<<304, 128, 0, s>>>(a, nullptr);
 }
 
-// Batched forms (one lattice for every cell of a batch).
+// Batched forms (one lattice for every cell of a batch; walls: some cell has them).
 template <typename S>
-void launch_stash_fix_batch(int lattice, const StashFixArgs* cells, int nc, cudaStream_t s)
+void launch_is_save_batch(int lattice, const ISFixArgs* cells, int nc, cudaStream_t s)
 {
     const dim3 grid(std::max(2, 256 / nc), nc);
-    if (lattice == 0) k_stash_fix<D2Q9, S, true><<<grid, 128, 0, s>>>(StashFixArgs{}, cells);
-    else k_stash_fix<D3Q19, S, true><<<grid, 128, 0, s>>>(StashFixArgs{}, cells);
+    if (lattice == 0) launch_is_save_l<D2Q9, S, true>(ISFixArgs{}, cells, grid, true, s);
+    else launch_is_save_l<D3Q19, S, true>(ISFixArgs{}, cells, grid, true, s);
+}
+
+template <typename S>
+void launch_is_fix_batch(int lattice, const ISFixArgs* cells, int nc, cudaStream_t s)
+{
+    const dim3 grid(std::max(2, 256 / nc), nc);
+    if (lattice == 0) k_is_fix<D2Q9, S, true><<<grid, 128, 0, s>>>(ISFixArgs{}, cells);
+    else k_is_fix<D3Q19, S, true><<<grid, 128, 0, s>>>(ISFixArgs{}, cells);
 }
 
 template <typename S>
@@ -1039,9 +1166,11 @@ const KernelTable* make_table()
                                   launch_convert_in<S>,
                                   launch_unstream<S>,
                                   launch_fill_rest<S>,
-                                  launch_stash_fix<S>,
+                                  launch_is_save<S>,
+                                  launch_is_fix<S>,
                                   launch_sweep_batch<S>,
-                                  launch_stash_fix_batch<S>,
+                                  launch_is_save_batch<S>,
+                                  launch_is_fix_batch<S>,
                                   launch_update_masks_batch<S>,
                                   launch_features<S>,
                                   (int)sizeof(S),
