@@ -167,6 +167,16 @@ lbm_status lbm_get_info(lbm_ctx* ctx, long long out[6]);
  * synchronizes. Errors as lbm_step; LBM_E_INVALID if n < 1 or out_ms is NULL. */
 lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3]);
 
+/* Shape of the main sweep kernel (a tuning knob; results agree to FP32 rounding). For the
+ * FP32 / FP16 / BF16 storages on a lattice with even nx, threads_x = 16, 32, 64 or 128
+ * selects the two-site kernel (each thread updates the sites x, x + 1 with paired 8- or
+ * 4-byte accesses and packed FP32 pair arithmetic; blocks of 128 threads, threads_x of them
+ * along x, 128 / threads_x rows); 0 selects the one-site kernel; -1 (the default) picks
+ * the one-site kernel for FP32 storage and the two-site kernel with 16 threads along x for
+ * FP16 / BF16 storage. FP64 storage always uses the one-site kernel. Drops the captured
+ * step graphs. LBM_E_INVALID for other values. */
+lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x);
+
 /* Largest particle count lbm_bs_exchange_noalloc accepts. */
 #define LBM_NOALLOC_MAX_PARTICLES 65536
 
@@ -218,7 +228,8 @@ lbm_status lbm_bs_exchange_noalloc(int lattice, int nx, int ny, int nz, const in
  * launch over all cells (a schedule table of 128-thread tiles, each tile one rectangle of
  * one x-y plane of one cell) and one launch per particle-phase kernel (the cell as the
  * second grid index), captured in CUDA graphs of one or several steps. Each cell's result
- * is bit for bit the result of stepping it alone. */
+ * is bit for bit the result of stepping it alone with the one-site sweep kernel
+ * (lbm_set_sweep_shape(ctx, 0)); the batch sweep is that kernel. */
 
 /* Creates ncells contexts sharing the lattice, storage precision, face kinds, particle
  * gravity, contact gap and force-on-particles flag (meaning as lbm_configure); dims

@@ -1,10 +1,11 @@
 """Builds the CUDA library ``liblbmp.so`` in-tree for sm_103a (GB300).
 
-Seven translation units are compiled in parallel with nvcc, one ``-gencode`` each:
+Nine translation units are compiled in parallel with nvcc, one ``-gencode`` each:
 ``api.cu`` (host C-ABI; host code with -ffp-contract=off), ``sweep_f64.cu`` and
 ``particles.cu`` (-fmad=false: FP64 arithmetic evaluated exactly as written),
-``sweep_lp.cu`` (FP32 / FP16 / BF16 storage), ``noalloc.cu`` (the allocation-free boundary-site
-exchange), ``batch.cu`` (batched ensembles), ``mlp.cu`` (the closure network). Output: ``paper_1105_2904_gb300/_lib/``.
+``sweep_f32.cu``, ``sweep_f16.cu``, ``sweep_bf16.cu`` (FP32 / FP16 / BF16 storage),
+``noalloc.cu`` (the allocation-free boundary-site exchange), ``batch.cu`` (batched
+ensembles), ``mlp.cu`` (the closure network). Output: ``paper_1105_2904_gb300/_lib/``.
 """
 from __future__ import annotations
 
@@ -28,7 +29,9 @@ UNITS = {
     "api.cu": [],
     "sweep_f64.cu": ["-fmad=false"],
     "particles.cu": ["-fmad=false"],
-    "sweep_lp.cu": [],
+    "sweep_f32.cu": [],
+    "sweep_f16.cu": [],
+    "sweep_bf16.cu": [],
     "noalloc.cu": [],
     "batch.cu": [],
     "mlp.cu": [],

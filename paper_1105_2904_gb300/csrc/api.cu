@@ -221,6 +221,9 @@ SweepArgs sweep_args(lbm_ctx* ctx, int c)
     a.pre_f = (float)a.pre;
     for (int k = 0; k < 3; ++k) a.F_f[k] = (float)ctx->F[k];
     wall_args(ctx, a);
+    // automatic shape: measured fastest per storage at the 512^3 suspension (FP32: one-site)
+    const bool half = ctx->precision == LBM_FP16DEV || ctx->precision == LBM_BF16DEV;
+    a.pair_bx = ctx->sweep_bx < 0 ? (half ? 16 : 0) : ctx->sweep_bx;
     return a;
 }
 
@@ -668,6 +671,22 @@ lbm_status lbm_step(lbm_ctx* ctx, int n)
         ctx->cur ^= 1;
         ++ctx->steps;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x)
+{
+    if (!ctx) return LBM_E_INVALID;
+    if (!(threads_x == -1 || threads_x == 0 || threads_x == 16 || threads_x == 32 || threads_x == 64 ||
+          threads_x == 128))
+        return fail(ctx, LBM_E_INVALID, "sweep shape: threads_x must be -1, 0, 16, 32, 64 or 128");
+    if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+    ctx->sweep_bx = threads_x;
+    for (auto& ge : ctx->gexec)
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
     return LBM_OK;
 }
 

@@ -25,6 +25,7 @@ struct lbm_ctx {
     lbmp::Geom g{};
     double tau = 0.6, F[3] = {0, 0, 0};
     int precision = LBM_FP32;
+    int sweep_bx = -1;         // lbm_set_sweep_shape
     const lbmp::KernelTable* kt = nullptr;
     double grav[3] = {0, 0, 0};
     double uw[6][3] = {};      // tangential velocity of each wall face (host copy)

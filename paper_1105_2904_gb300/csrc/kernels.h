@@ -23,6 +23,8 @@ struct SweepArgs {
     float omega_f, pre_f, F_f[3];  // the same in FP32 (reduced-storage sweeps)
     int moving_walls;          // 1: wall faces may move (uw is read)
     const WallVel* uw;         // wall velocities of the streaming that the pull completes
+    int pair_bx;               // deviation storage, even nx: two-site kernel with this many
+                               // threads along x (16, 32, 64 or 128); 0: one-site kernel
 };
 
 struct MaterializeArgs {

@@ -1,5 +1,6 @@
 // The fused lattice sweep and its companions, templated on the lattice and the storage
-// format. Included by sweep_f64.cu (built with -fmad=false) and sweep_lp.cu.
+// format. Included by sweep_f64.cu (built with -fmad=false) and sweep_f32.cu, sweep_f16.cu,
+// sweep_bf16.cu.
 //
 // Pull scheme: buffer `fin` holds the post-collision populations of the previous step at
 // the sites where they were computed, so site x gathers f_i(x) = fin_i(x - c_i), or
@@ -495,6 +496,33 @@ __global__ void k_update_masks(const MaskArgs a0, const MaskArgs* __restrict__ c
     }
 }
 
+// BS transfer of one site in the deviation form (Eqs. 5-7): the forced collision keeps the
+// density and adds F to the momentum, so the post-collision rho_B and rho_B u_B are rho and
+// j + F of the pulled values (mrho, mj). The site takes f^eq(rho_B, u_p + omega_p x r) and
+// its per-site record (dp = rho_B (u_B' - u_B) = rho_B u_B' - (j + F), dl = r x dp, the
+// owner's tag and the step id: one aligned 32-byte sector) feeds the per-particle sums
+// (Eqs. 8-9) that the particle phase takes afterwards in a fixed order.
+template <class L>
+__device__ __forceinline__ void bs_transfer_dev(const SweepArgs& a, int x, int y, int z, unsigned idx, unsigned tagx,
+                                                float mrho, float mj0, float mj1, float mj2, float f[])
+{
+    const PKernF k = a.pv.pkf[tagx & PID_MASK];
+    float r[3], ubp[3], dv[6];
+    lever_arm(a.g, k, x, y, z, r);
+    rigid_velocity(k, r, ubp);
+    const float rho = 1.0f + mrho;
+    const float pB[3] = {mj0 + a.F_f[0], mj1 + a.F_f[1], mj2 + a.F_f[2]};
+    equilibrium_dev<L>(mrho, ubp, f);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dv[q] = rho * ubp[q] - pB[q];
+    dv[3] = r[1] * dv[2] - r[2] * dv[1];
+    dv[4] = r[2] * dv[0] - r[0] * dv[2];
+    dv[5] = r[0] * dv[1] - r[1] * dv[0];
+    float4* sc = (float4*)a.bs_scratch + (size_t)idx * 2;
+    sc[0] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+    sc[1] = make_float4(dv[4], dv[5], __uint_as_float(tagx), __uint_as_float(*a.pv.step_id));
+}
+
 // Everything a site does after its populations are pulled: the pending IS imposition,
 // the collision, the BS transfer and its per-site record, and the stores (IS sites store
 // their density in every slot). RESTORE: store an IS site's populations instead (the
@@ -534,77 +562,43 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
         collide_plain<L>(f, a);
 
     if constexpr (PART) {
-        const unsigned cls = tagx >> 30;
         // Particle-fluid momentum transfer at BS sites (Eqs. 5-7).
-        C dv[6] = {0, 0, 0, 0, 0, 0};
-        const bool isbs = valid && cls == CLS_BS;
-        if (isbs) {
+        const bool isbs = valid && (tagx >> 30) == CLS_BS;
+        if constexpr (St::deviation) {
+            if (isbs) bs_transfer_dev<L>(a, x, y, z, idx, tagx, mrho, mj0, mj1, mj2, f);
+        } else if (isbs) {
             C r[3], ub[3], ubp[3], du[3];
-            if constexpr (St::deviation) {
-                const PKernF k = a.pv.pkf[tagx & PID_MASK];
-                lever_arm(g, k, x, y, z, r);
-                rigid_velocity(k, r, ubp);
-            } else {
-                const PKern& k = a.pv.pk[tagx & PID_MASK];
-                lever_arm(g, k, x, y, z, r);
-                rigid_velocity(k, r, ubp);
-            }
-            if constexpr (St::deviation) {
-                // The forced collision keeps the density and adds F to the momentum, so the
-                // post-collision rho_B and rho_B u_B are rho and j + F of the pulled values.
-                const float drho = mrho;
-                const float rho = 1.0f + drho;
-                const float pB[3] = {mj0 + a.F_f[0], mj1 + a.F_f[1], mj2 + a.F_f[2]};
-                equilibrium_dev<L>(drho, ubp, f);
-                // dp = rho_B (u_B' - u_B) = rho u_B' - (j + F); dl = r x dp (Eqs. 6-7)
+            const PKern& k = a.pv.pk[tagx & PID_MASK];
+            lever_arm(g, k, x, y, z, r);
+            rigid_velocity(k, r, ubp);
+            double rhoB = 0.0;
+            sfor<0, Q>([&](auto ic) { rhoB += f[decltype(ic)::value]; });
+            double jB[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-                for (int q = 0; q < 3; ++q) dv[q] = rho * ubp[q] - pB[q];
-                dv[3] = r[1] * dv[2] - r[2] * dv[1];
-                dv[4] = r[2] * dv[0] - r[0] * dv[2];
-                dv[5] = r[0] * dv[1] - r[1] * dv[0];
-                (void)ub;
-                (void)du;
-            } else {
-                double rhoB = 0.0;
-                sfor<0, Q>([&](auto ic) { rhoB += f[decltype(ic)::value]; });
-                double jB[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    sfor<0, Q>([&](auto ic) {
-                        constexpr int i = decltype(ic)::value;
-                        jB[q] += f[i] * (double)L::c(i, q);
-                    });
-#pragma unroll
-                for (int q = 0; q < 3; ++q) ub[q] = jB[q] / rhoB;
+            for (int q = 0; q < 3; ++q)
                 sfor<0, Q>([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    f[i] = feq_plain<L, i>(1.0, rhoB, ubp);
+                    jB[q] += f[i] * (double)L::c(i, q);
                 });
 #pragma unroll
-                for (int q = 0; q < 3; ++q) du[q] = ubp[q] - ub[q];
-                double cr[3];
-                cr[0] = r[1] * du[2] - r[2] * du[1];
-                cr[1] = r[2] * du[0] - r[0] * du[2];
-                cr[2] = r[0] * du[1] - r[1] * du[0];
+            for (int q = 0; q < 3; ++q) ub[q] = jB[q] / rhoB;
+            sfor<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                f[i] = feq_plain<L, i>(1.0, rhoB, ubp);
+            });
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    dv[q] = rhoB * du[q];
-                    dv[3 + q] = rhoB * cr[q];
-                }
-            }
-        }
-        // Per-site contributions; the per-particle sums (Eqs. 8-9) are taken afterwards in
-        // a fixed order by the particle phase.
-        if (isbs) {
-            if constexpr (St::deviation) {
-                // one aligned 32-byte record per site: dp, dl and the owner's id
-                float4* sc = (float4*)a.bs_scratch + (size_t)idx * 2;
-                sc[0] = make_float4(dv[0], dv[1], dv[2], dv[3]);
-                sc[1] = make_float4(dv[4], dv[5], __uint_as_float(tagx), __uint_as_float(*a.pv.step_id));
-            } else {
-                C* sc = (C*)a.bs_scratch + (size_t)idx * 6;
+            for (int q = 0; q < 3; ++q) du[q] = ubp[q] - ub[q];
+            double cr[3];
+            cr[0] = r[1] * du[2] - r[2] * du[1];
+            cr[1] = r[2] * du[0] - r[0] * du[2];
+            cr[2] = r[0] * du[1] - r[1] * du[0];
+            // Per-site contributions; the per-particle sums (Eqs. 8-9) are taken afterwards
+            // in a fixed order by the particle phase.
+            C* sc = (C*)a.bs_scratch + (size_t)idx * 6;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) sc[q] = dv[q];
+            for (int q = 0; q < 3; ++q) {
+                sc[q] = rhoB * du[q];
+                sc[3 + q] = rhoB * cr[q];
             }
         }
     }
@@ -1000,10 +994,24 @@ __global__ void k_is_fix(const ISFixArgs a0, const ISFixArgs* __restrict__ cells
     }
 }
 
+}  // namespace lbmp
+
+#include "sweep2.cuh"
+
+namespace lbmp {
+
 // ---- launchers --------------------------------------------------------------------------
+// Deviation storages with an even nx take the two-site kernel (a.pair_bx threads along x),
+// everything else the one-site kernel.
 template <class L, typename S, bool WALLS, bool PART>
 void launch_sweep_v(const SweepArgs& a, cudaStream_t s)
 {
+    if constexpr (Store<S>::deviation) {
+        if (a.pair_bx > 0 && a.g.nx % 2 == 0) {
+            launch_sweep2_v<L, S, WALLS, PART>(a, a.pair_bx, s);
+            return;
+        }
+    }
     const dim3 grid((a.g.nx + SWEEP_THREADS - 1) / SWEEP_THREADS, a.g.ny, a.g.nz);
     k_sweep<L, S, WALLS, PART><<<grid, SWEEP_THREADS, 0, s>>>(a);
 }

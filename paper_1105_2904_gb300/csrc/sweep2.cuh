@@ -1,0 +1,282 @@
+// Two-site form of the fused sweep for the deviation storages (FP32, FP16, BF16): each thread
+// owns a pair of x-neighbouring sites (x0, x0 + 1), x0 even. Populations move as aligned
+// pairs (8-byte float2 or 4-byte half2 / bfloat162 accesses) wherever the pull source is the
+// same pair of another row, and the collision runs on both sites at once with the packed
+// FP32 pair instructions of sm_100+ (FFMA2 / FADD2 / FMUL2). Sites inside particles take the
+// same per-site steps as the one-site kernel (IS imposition, BS transfer, density carry),
+// applied to each half of the pair. Requires an even nx.
+#pragma once
+
+#include "sweep.cuh"
+
+namespace lbmp {
+
+// ---- packed FP32 pairs ---------------------------------------------------------------------
+__device__ __forceinline__ float2 p2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, p2(-1.0f), a); }
+
+// ---- storage pairs -------------------------------------------------------------------------
+// Aligned loads and stores of two consecutive elements, converted to and from the compute
+// form (the deviation g = f - w) exactly as Store<S>::load / save convert one element.
+template <typename S> struct Pair;
+template <> struct Pair<float> {
+    __device__ static float2 load(const float* p, float) { return *reinterpret_cast<const float2*>(p); }
+    __device__ static void store(float* p, float2 g, float) { *reinterpret_cast<float2*>(p) = g; }
+    __device__ static float2 round(float2 g, float) { return g; }
+};
+template <> struct Pair<__half> {
+    __device__ static float2 load(const __half* p, float w)
+    {
+        return mul2(__half22float2(*reinterpret_cast<const __half2*>(p)), p2(w));
+    }
+    __device__ static __half2 pack(float2 g, float w) { return __float22half2_rn(mul2(g, p2(1.0f / w))); }
+    __device__ static void store(__half* p, float2 g, float w) { *reinterpret_cast<__half2*>(p) = pack(g, w); }
+    __device__ static float2 round(float2 g, float w) { return mul2(__half22float2(pack(g, w)), p2(w)); }
+};
+template <> struct Pair<__nv_bfloat16> {
+    __device__ static float2 load(const __nv_bfloat16* p, float w)
+    {
+        return mul2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)), p2(w));
+    }
+    __device__ static __nv_bfloat162 pack(float2 g, float w) { return __float22bfloat162_rn(mul2(g, p2(1.0f / w))); }
+    __device__ static void store(__nv_bfloat16* p, float2 g, float w)
+    {
+        *reinterpret_cast<__nv_bfloat162*>(p) = pack(g, w);
+    }
+    __device__ static float2 round(float2 g, float w) { return mul2(__bfloat1622float2(pack(g, w)), p2(w)); }
+};
+
+// Component h (0: site x0, 1: site x0 + 1) of a pair.
+template <int H> __device__ __forceinline__ float& half_of(float2& v) { if constexpr (H == 0) return v.x; else return v.y; }
+
+// Neighbours of the pair: n0 for site x0 (x0 + 1 never wraps), n1 for site x0 + 1.
+template <bool WALLS>
+__device__ __forceinline__ void pair_neighbours(const Geom& g, int x0, int y, int z, Nbr& n0, Nbr& n1)
+{
+    n0 = neighbours<WALLS>(g, x0, y, z);
+    n1 = n0;
+    n1.xm = x0;
+    n1.bxm = false;
+    n1.xp = x0 + 2;
+    n1.bxp = false;
+    if (n1.xp >= g.nx) {
+        n1.xp -= g.nx;
+        if (WALLS) n1.bxp = g.wall[0];
+    }
+}
+
+// Gathers the populations of both sites (pull propagation with bounce-back): a pair load
+// when both sources are the same pair of another row (c_x = 0), two loads otherwise.
+template <class L, typename S, bool WALLS>
+__device__ __forceinline__ void pull2(const S* __restrict__ fin, const Geom& g, const Nbr& n0, const Nbr& n1,
+                                      int x0, int y, int z, unsigned idx, float2 f[])
+{
+    using St = Store<S>;
+    const size_t N = g.N;
+    sfor<0, L::Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        constexpr float w = (float)L::w(i);
+        const int sy = cy > 0 ? n0.ym : (cy < 0 ? n0.yp : y);
+        const int sz = cz > 0 ? n0.zm : (cz < 0 ? n0.zp : z);
+        bool brow = false;
+        if constexpr (WALLS)
+            brow = (cy > 0 && n0.bym) || (cy < 0 && n0.byp) || (cz > 0 && n0.bzm) || (cz < 0 && n0.bzp);
+        const unsigned row = ((unsigned)sz * (unsigned)g.ny + (unsigned)sy) * (unsigned)g.nx;
+        const S* own = fin + (size_t)L::opp(i) * N + idx;  // bounced: the site itself, opp(i)
+        if constexpr (cx == 0) {
+            f[i] = brow ? Pair<S>::load(own, w) : Pair<S>::load(fin + (size_t)i * N + row + (unsigned)x0, w);
+        } else {
+            // source x - c_x of each site; a wall on x bounces only the site beside it
+            const int sx0 = cx > 0 ? n0.xm : x0 + 1;
+            const int sx1 = cx > 0 ? x0 : n1.xp;
+            bool b0 = brow, b1 = brow;
+            if constexpr (WALLS) {
+                b0 = b0 || (cx > 0 && n0.bxm);
+                b1 = b1 || (cx < 0 && n1.bxp);
+            }
+            const S* p0 = b0 ? own : fin + (size_t)i * N + row + (unsigned)sx0;
+            const S* p1 = b1 ? own + 1 : fin + (size_t)i * N + row + (unsigned)sx1;
+            f[i] = make_float2(St::load(*p0, w), St::load(*p1, w));
+        }
+    });
+}
+
+// BGK collision with Guo forcing (Eq. 3) of both sites on packed pairs; the same expression
+// as collide_dev, one instruction for two sites.
+template <class L>
+__device__ __forceinline__ void collide_dev2(float2 g[], const SweepArgs& a, float2& drho, float2& j0, float2& j1,
+                                             float2& j2)
+{
+    constexpr int Q = L::Q;
+    drho = g[0];
+    j0 = j1 = j2 = p2(0.0f);
+    sfor<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        drho = add2(drho, g[i]);
+        if constexpr (L::c(i, 0) > 0) j0 = add2(j0, g[i]);
+        if constexpr (L::c(i, 0) < 0) j0 = sub2(j0, g[i]);
+        if constexpr (L::c(i, 1) > 0) j1 = add2(j1, g[i]);
+        if constexpr (L::c(i, 1) < 0) j1 = sub2(j1, g[i]);
+        if constexpr (L::c(i, 2) > 0) j2 = add2(j2, g[i]);
+        if constexpr (L::c(i, 2) < 0) j2 = sub2(j2, g[i]);
+    });
+    const float F0 = a.F_f[0], F1 = a.F_f[1], F2 = a.F_f[2];
+    const float2 rho = add2(drho, p2(1.0f));
+    const float2 inv = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    const float2 u0 = mul2(add2(j0, p2(0.5f * F0)), inv);
+    const float2 u1 = mul2(add2(j1, p2(0.5f * F1)), inv);
+    const float2 u2 = mul2(add2(j2, p2(0.5f * F2)), inv);
+    const float omega = a.omega_f, pre = a.pre_f, om1 = 1.0f - omega;
+    const float2 uF3 = mul2(p2(3.0f), fma2(u2, p2(F2), fma2(u1, p2(F1), mul2(u0, p2(F0)))));
+    const float2 usq15 = mul2(p2(1.5f), fma2(u2, u2, fma2(u1, u1, mul2(u0, u0))));
+    {   // rest direction
+        const float w = (float)L::w(0);
+        const float2 e = fma2(rho, mul2(usq15, p2(-1.0f)), drho);  // drho - rho usq15
+        g[0] = fma2(p2(om1), g[0], fma2(p2(omega * w), e, mul2(p2(-pre * w), uF3)));
+    }
+    sfor<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int j = L::opp(i);
+        if constexpr (j > i) {
+            constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+            float2 cu = p2(0.0f);
+            bool first = true;
+            auto acc = [&](int c, float2 v) {
+                if (c == 0) return;
+                if (first) {
+                    cu = c > 0 ? v : mul2(v, p2(-1.0f));
+                    first = false;
+                } else {
+                    cu = c > 0 ? add2(cu, v) : sub2(cu, v);
+                }
+            };
+            acc(cx, u0);
+            acc(cy, u1);
+            acc(cz, u2);
+            const float cF = (float)cx * F0 + (float)cy * F1 + (float)cz * F2;
+            const float w = (float)L::w(i);
+            const float ow = omega * w, pw = pre * w;
+            // A = ow (drho + rho (4.5 cu^2 - 1.5 u^2)) + pw (9 cu cF - 3 u.F)
+            const float2 q = fma2(mul2(cu, cu), p2(4.5f), mul2(usq15, p2(-1.0f)));
+            const float2 A = fma2(p2(ow), fma2(rho, q, drho), mul2(p2(pw), fma2(cu, p2(9.0f * cF), mul2(uF3, p2(-1.0f)))));
+            // B = 3 (ow rho cu + pw cF)
+            const float2 B = mul2(p2(3.0f), fma2(mul2(p2(ow), rho), cu, p2(pw * cF)));
+            g[i] = fma2(p2(om1), g[i], add2(A, B));
+            g[j] = fma2(p2(om1), g[j], sub2(A, B));
+        }
+    });
+}
+
+template <class L, typename S, bool WALLS, bool PART, int H>
+__device__ __forceinline__ void particle_pre_half(const SweepArgs& a, const Nbr& n, int x, int y, int z,
+                                                  unsigned tagx, unsigned mask, float2 f[])
+{
+    constexpr int Q = L::Q;
+    float fs[Q];
+    sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = half_of<H>(f[decltype(ic)::value]); });
+    if constexpr (PART) {
+        if (*a.pv.pending) {
+            const unsigned m = tagx != TAG_FLUID ? mask : 0u;
+            substitute_is_dev<L, WALLS>(a.g, n, x, y, z, m, tagx & PID_MASK, a.pv, fs);
+        }
+    }
+    if constexpr (WALLS) {
+        if (a.moving_walls && *a.pv.pending) wall_momentum<L, float, WALLS>(n, a.uw->uf, fs);
+    }
+    sfor<0, Q>([&](auto ic) { half_of<H>(f[decltype(ic)::value]) = fs[decltype(ic)::value]; });
+}
+
+template <class L, int H>
+__device__ __forceinline__ void bs_half(const SweepArgs& a, int x, int y, int z, unsigned idx, unsigned tagx,
+                                        float2 mrho, float2 mj0, float2 mj1, float2 mj2, float2 f[])
+{
+    constexpr int Q = L::Q;
+    float fs[Q];
+    sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = half_of<H>(f[decltype(ic)::value]); });
+    bs_transfer_dev<L>(a, x, y, z, idx, tagx, half_of<H>(mrho), half_of<H>(mj0), half_of<H>(mj1), half_of<H>(mj2),
+                       fs);
+    sfor<0, Q>([&](auto ic) { half_of<H>(f[decltype(ic)::value]) = fs[decltype(ic)::value]; });
+}
+
+// One block: BX threads along x (2 BX sites) times 128 / BX rows of one z-plane.
+template <class L, typename S, bool WALLS, bool PART, int BX>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep2(const SweepArgs a)
+{
+    constexpr int Q = L::Q;
+    constexpr int BY = SWEEP_THREADS / BX;
+    const Geom& g = a.g;
+    const int tx = (int)threadIdx.x % BX, ty = (int)threadIdx.x / BX;
+    const int xr = (int)blockIdx.x * (2 * BX) + 2 * tx;
+    const int yr = (int)blockIdx.y * BY + ty;
+    const int z = (int)blockIdx.z;
+    const bool valid = xr < g.nx && yr < g.ny;
+    const int x0 = min(xr, g.nx - 2), y = min(yr, g.ny - 1);
+    const unsigned idx = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x0;
+    Nbr n0, n1;
+    pair_neighbours<WALLS>(g, x0, y, z, n0, n1);
+    uint2 tg = make_uint2(TAG_FLUID, TAG_FLUID), mk = make_uint2(0u, 0u);
+    if constexpr (PART) {
+        tg = *reinterpret_cast<const uint2*>(a.pv.tag + idx);
+        mk = *reinterpret_cast<const uint2*>(a.pv.ismask + idx);
+    }
+    float2 f[Q];
+    pull2<L, S, WALLS>((const S*)a.fin, g, n0, n1, x0, y, z, idx, f);
+    if constexpr (PART || WALLS) {
+        particle_pre_half<L, S, WALLS, PART, 0>(a, n0, x0, y, z, tg.x, mk.x, f);
+        particle_pre_half<L, S, WALLS, PART, 1>(a, n1, x0 + 1, y, z, tg.y, mk.y, f);
+    }
+    float2 mrho, mj0, mj1, mj2;
+    collide_dev2<L>(f, a, mrho, mj0, mj1, mj2);
+    bool any_is = false;
+    bool is0 = false, is1 = false;
+    if constexpr (PART) {
+        if (valid && (tg.x >> 30) == CLS_BS) bs_half<L, 0>(a, x0, y, z, idx, tg.x, mrho, mj0, mj1, mj2, f);
+        if (valid && (tg.y >> 30) == CLS_BS) bs_half<L, 1>(a, x0 + 1, y, z, idx + 1, tg.y, mrho, mj0, mj1, mj2, f);
+        is0 = (tg.x >> 30) == CLS_IS;
+        is1 = (tg.y >> 30) == CLS_IS;
+        any_is = __any_sync(0xFFFFFFFFu, is0 || is1);
+    }
+    if (!valid) return;
+    S* __restrict__ fout = (S*)a.fout;
+    const size_t N = g.N;
+    if (any_is) {
+        // density carry: an IS site stores its post-collision density (the sum of its values
+        // as stored) in every slot
+        float2 dens = p2(0.0f);
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            dens = add2(dens, Pair<S>::round(f[i], (float)L::w(i)));
+        });
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            float2 v = f[i];
+            if (is0) v.x = dens.x;
+            if (is1) v.y = dens.y;
+            Pair<S>::store(fout + (size_t)i * N + idx, v, (float)L::w(i));
+        });
+    } else {
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            Pair<S>::store(fout + (size_t)i * N + idx, f[i], (float)L::w(i));
+        });
+    }
+}
+
+template <class L, typename S, bool WALLS, bool PART>
+void launch_sweep2_v(const SweepArgs& a, int bx, cudaStream_t s)
+{
+    const int by = SWEEP_THREADS / bx;
+    const dim3 grid((a.g.nx + 2 * bx - 1) / (2 * bx), (a.g.ny + by - 1) / by, a.g.nz);
+    switch (bx) {
+    case 16: k_sweep2<L, S, WALLS, PART, 16><<<grid, SWEEP_THREADS, 0, s>>>(a); break;
+    case 32: k_sweep2<L, S, WALLS, PART, 32><<<grid, SWEEP_THREADS, 0, s>>>(a); break;
+    case 64: k_sweep2<L, S, WALLS, PART, 64><<<grid, SWEEP_THREADS, 0, s>>>(a); break;
+    default: k_sweep2<L, S, WALLS, PART, 128><<<grid, SWEEP_THREADS, 0, s>>>(a); break;
+    }
+}
+
+}  // namespace lbmp

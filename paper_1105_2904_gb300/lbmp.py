@@ -25,7 +25,7 @@ LBM_PERIODIC, LBM_NOSLIP = 0, 1
 
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
-            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_bs_exchange_noalloc",
+            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_set_sweep_shape", "lbm_bs_exchange_noalloc",
             "lbm_last_error", "lbm_destroy",
             "lbm_batch_create", "lbm_batch_add_particles", "lbm_batch_cell", "lbm_batch_set_tuning",
             "lbm_batch_step", "lbm_batch_synchronize", "lbm_batch_profile_steps", "lbm_batch_get_info",
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_get_masks.argtypes = [P, ctypes.POINTER(ctypes.c_uint)]
     lib.lbm_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.lbm_profile_steps.argtypes = [P, i32, D]
+    lib.lbm_set_sweep_shape.argtypes = [P, i32]
     lib.lbm_bs_exchange_noalloc.argtypes = [i32, i32, i32, i32, I, D, P, P, i32, P, P, P, P, P, P]
     lib.lbm_last_error.argtypes = [P]
     lib.lbm_last_error.restype = ctypes.c_char_p
@@ -224,6 +225,10 @@ def lbm_profile_steps(h, n):
     out = np.zeros(3)
     _check(h, load().lbm_profile_steps(h, int(n), _dp(out)))
     return {"sweep_ms": float(out[0]), "particle_ms": float(out[1]), "step_ms": float(out[2])}
+
+
+def lbm_set_sweep_shape(h, threads_x):
+    _check(h, load().lbm_set_sweep_shape(h, int(threads_x)))
 
 
 def lbm_bs_exchange_noalloc(lattice, nx, ny, nz, walls, body_force, g_ptr, tags_ptr, n, centers_ptr,
@@ -430,6 +435,11 @@ class Simulation:
 
     def profile(self, n):
         return lbm_profile_steps(self.h, n)
+
+    def set_sweep_shape(self, threads_x):
+        """Sweep kernel shape (lbm_set_sweep_shape): 16, 32, 64, 128 threads along x for the
+        two-site kernel, 0 for the one-site kernel, -1 automatic."""
+        lbm_set_sweep_shape(self.h, threads_x)
 
     def closure_features(self, n_side, spacing, u_ref):
         """Closure inputs of every particle as a CUDA float32 tensor [np, n_side^3 * 4]."""

@@ -3,9 +3,9 @@
 - FP64 storage: each cell of a batch matches its own FP64 oracle run to 1e-12 relative
   (fields, particle trajectories, force and torque) and bit for bit on the owner map.
 - FP32 / FP16 storage: each cell of a batch is bit for bit the same as the same cell stepped
-  alone as a single context, under every launch tuning (tile widths, schedule orders,
-  persistent grids, multi-step graphs): the batch changes how the work is launched, not
-  what is computed.
+  alone as a single context with the one-site sweep kernel, under every launch tuning (tile
+  widths, schedule orders, persistent grids, multi-step graphs): the batch changes how the
+  work is launched, not what is computed.
 - Cells without particles, walls, and the buffer-parity rule.
 """
 import numpy as np
@@ -76,6 +76,7 @@ def _separate(e, precision, steps, walls=(0, 0, 0), gravity=(0, 0, 0)):
         nx, ny, nz = e.dims[k]
         s = lbmp.Simulation(O.D3Q19, nx, ny, nz, e.taus[k], body_force=e.body_force, precision=precision,
                             walls=walls, gravity=gravity, gap=0.5, body_force_on_particles=e.body_force_on_particles)
+        s.set_sweep_shape(0)   # the batch runs the one-site sweep of every cell
         if len(e.radii[k]):
             s.add_particles(e.centers[k], e.radii[k], e.densities[k], e.velocities[k])
         s.step(steps)
