@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--workload", default="d3q19_512", choices=["d3q19_512", "d2q9_sedimentation", "ensemble_64"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     p.add_argument("--edge", type=int, default=0, help="override the 3D box edge (same solid fraction)")
+    p.add_argument("--sweep-shape", type=int, default=-1,
+                   help="sweep kernel shape (lbm_set_sweep_shape): -1 automatic, 0 one-site, 16/32/64/128 two-site")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -259,6 +261,7 @@ def run_ours(args):
         sim = lbmp.Simulation(lattice, nx, ny, nz, wl.tau, body_force=wl.body_force, precision=args.precision,
                               walls=wl.walls, gravity=wl.gravity, gap=0.0,
                               body_force_on_particles=wl.body_force_on_particles, cuda_stream=stream.cuda_stream)
+        sim.set_sweep_shape(args.sweep_shape)
         sim.add_particles(c, r, d, v)
         return sim
 

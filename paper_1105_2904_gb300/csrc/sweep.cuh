@@ -362,6 +362,10 @@ __device__ __forceinline__ bool pull_bounces(const Nbr& n)
     }
 }
 
+template <class L, bool WALLS>
+__device__ __forceinline__ void substitute_is_other_dev(const Geom& g, const Nbr& n, int x, int y, int z, unsigned owner,
+                                                     const PartView& pv, float f[]);
+
 // FP32 form. With u(s) = u(x) - omega x c_i for the source s = x - c_i of a rigid motion:
 // c_i.u(s) = c_i.u(x) (c_i.(omega x c_i) = 0) and
 // |u(s)|^2 = |u(x)|^2 - 2 c_i.(u(x) x omega) + |omega|^2 |c_i|^2 - (omega.c_i)^2,
@@ -425,8 +429,17 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
             }
         });
     }
-    if (m & MASK_OTHER) {
-        // Sources owned by another particle (site sets of close particles meet): rare.
+    if (m & MASK_OTHER) substitute_is_other_dev<L, WALLS>(g, n, x, y, z, owner, pv, f);
+}
+
+// Sources owned by another particle than the site's own (site sets of close particles
+// meet): rare, one direction at a time.
+template <class L, bool WALLS>
+__device__ __forceinline__ void substitute_is_other_dev(const Geom& g, const Nbr& n, int x, int y, int z, unsigned owner,
+                                                     const PartView& pv, float f[])
+{
+    constexpr int Q = L::Q;
+    {
 #pragma unroll 1
         for (int i = 0; i < Q; ++i) {
             const int cx = c_rt<L>(i, 0), cy = c_rt<L>(i, 1), cz = c_rt<L>(i, 2);

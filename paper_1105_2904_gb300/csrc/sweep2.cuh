@@ -171,35 +171,204 @@ __device__ __forceinline__ void collide_dev2(float2 g[], const SweepArgs& a, flo
     });
 }
 
-template <class L, typename S, bool WALLS, bool PART, int H>
-__device__ __forceinline__ void particle_pre_half(const SweepArgs& a, const Nbr& n, int x, int y, int z,
-                                                  unsigned tagx, unsigned mask, float2 f[])
+// Lever arms of both sites (each from its own owner's record) as pairs.
+template <typename K>
+__device__ __forceinline__ void lever_arm2(const Geom& g, const K& k0, const K& k1, int x0, int y, int z, float2 r[3])
+{
+    float r0[3], r1[3];
+    lever_arm(g, k0, x0, y, z, r0);
+    lever_arm(g, k1, x0 + 1, y, z, r1);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) r[q] = make_float2(r0[q], r1[q]);
+}
+
+// u_p + omega_p x r (Eqs. 5, 12) for both sites.
+__device__ __forceinline__ void rigid_velocity2(const float2 u[3], const float2 om[3], const float2 r[3], float2 out[3])
+{
+    out[0] = fma2(om[1], r[2], sub2(u[0], mul2(om[2], r[1])));
+    out[1] = fma2(om[2], r[0], sub2(u[1], mul2(om[0], r[2])));
+    out[2] = fma2(om[0], r[1], sub2(u[2], mul2(om[1], r[0])));
+}
+
+__device__ __forceinline__ void kin2(const PKernF& k0, const PKernF& k1, float2 u[3], float2 om[3])
+{
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        u[q] = make_float2(k0.u[q], k1.u[q]);
+        om[q] = make_float2(k0.om[q], k1.om[q]);
+    }
+}
+
+// c_i . v of a lattice direction on pairs (components 0 or +-1: adds only).
+template <class L, int i>
+__device__ __forceinline__ float2 cdot2(const float2 v[3])
+{
+    constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    float2 r = p2(0.0f);
+    bool first = true;
+    auto acc = [&](int c, float2 w) {
+        if (c == 0) return;
+        if (first) {
+            r = c > 0 ? w : mul2(w, p2(-1.0f));
+            first = false;
+        } else {
+            r = c > 0 ? add2(r, w) : sub2(r, w);
+        }
+    };
+    acc(cx, v[0]);
+    acc(cy, v[1]);
+    acc(cz, v[2]);
+    return r;
+}
+
+// The pending IS imposition (Eq. 12) for both sites of the pair, on packed pairs: the same
+// expression as substitute_is_dev (density carry: the pulled value is rho_I of its source),
+// each site with its own owner and IS-source mask. Warp-uniform; every lane calls it.
+template <class L, bool WALLS>
+__device__ __forceinline__ void substitute_is_dev2(const Geom& g, const Nbr& n0, const Nbr& n1, int x0, int y, int z,
+                                                   uint2 m, uint2 tags, const PartView& pv, float2 f[])
+{
+    constexpr int Q = L::Q;
+    const unsigned mm0 = m.x & ~MASK_OTHER, mm1 = m.y & ~MASK_OTHER;
+    const unsigned wm = __reduce_or_sync(__activemask(), mm0 | mm1);
+    if (wm) {
+        const PKernF k0 = pv.pkf[mm0 ? (tags.x & PID_MASK) : 0u];
+        const PKernF k1 = pv.pkf[mm1 ? (tags.y & PID_MASK) : 0u];
+        float2 r[3], u[3], om[3], ux[3];
+        lever_arm2(g, k0, k1, x0, y, z, r);
+        kin2(k0, k1, u, om);
+        rigid_velocity2(u, om, r, ux);
+        float2 a[3];  // u(x) x omega
+        a[0] = sub2(mul2(ux[1], om[2]), mul2(ux[2], om[1]));
+        a[1] = sub2(mul2(ux[2], om[0]), mul2(ux[0], om[2]));
+        a[2] = sub2(mul2(ux[0], om[1]), mul2(ux[1], om[0]));
+        const float2 usq = fma2(ux[2], ux[2], fma2(ux[1], ux[1], mul2(ux[0], ux[0])));
+        const float2 w2 = fma2(om[2], om[2], fma2(om[1], om[1], mul2(om[0], om[0])));
+        if (wm & 1u) {
+            const float2 E = mul2(p2(-1.5f), usq);
+            const float2 v = mul2(p2((float)L::w(0)), fma2(f[0], add2(E, p2(1.0f)), E));
+            if (mm0 & 1u) f[0].x = v.x;
+            if (mm1 & 1u) f[0].y = v.y;
+        }
+        sfor<1, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int j = L::opp(i);
+            if constexpr (j > i) {
+                constexpr unsigned pair = (1u << i) | (1u << j);
+                if (wm & pair) {
+                    constexpr float c2 = (float)(L::c(i, 0) * L::c(i, 0) + L::c(i, 1) * L::c(i, 1) + L::c(i, 2) * L::c(i, 2));
+                    constexpr float w = (float)L::w(i);
+                    const float2 cu = cdot2<L, i>(ux);
+                    const float2 ca = cdot2<L, i>(a);
+                    const float2 cw = cdot2<L, i>(om);
+                    const float2 base = sub2(fma2(w2, p2(c2), usq), mul2(cw, cw));
+                    const float2 S = fma2(mul2(cu, cu), p2(4.5f), mul2(base, p2(-1.5f)));
+                    const float2 D = mul2(p2(3.0f), add2(cu, ca));
+                    float2 Ei = add2(S, D), Ej = sub2(S, D);
+                    if constexpr (WALLS) {
+                        const float2 Sb = fma2(mul2(cu, cu), p2(4.5f), mul2(usq, p2(-1.5f)));
+                        const float2 cu3 = mul2(p2(3.0f), cu);
+                        if (pull_bounces<L, i, WALLS>(n0)) Ei.x = Sb.x - cu3.x;
+                        if (pull_bounces<L, i, WALLS>(n1)) Ei.y = Sb.y - cu3.y;
+                        if (pull_bounces<L, j, WALLS>(n0)) Ej.x = Sb.x + cu3.x;
+                        if (pull_bounces<L, j, WALLS>(n1)) Ej.y = Sb.y + cu3.y;
+                    }
+                    const float2 vi = mul2(p2(w), fma2(f[i], add2(Ei, p2(1.0f)), Ei));
+                    const float2 vj = mul2(p2(w), fma2(f[j], add2(Ej, p2(1.0f)), Ej));
+                    if (mm0 & (1u << i)) f[i].x = vi.x;
+                    if (mm1 & (1u << i)) f[i].y = vi.y;
+                    if (mm0 & (1u << j)) f[j].x = vj.x;
+                    if (mm1 & (1u << j)) f[j].y = vj.y;
+                }
+            }
+        });
+    }
+    if ((m.x | m.y) & MASK_OTHER) {
+        float fs[Q];
+        if (m.x & MASK_OTHER) {
+            sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = f[decltype(ic)::value].x; });
+            substitute_is_other_dev<L, WALLS>(g, n0, x0, y, z, tags.x & PID_MASK, pv, fs);
+            sfor<0, Q>([&](auto ic) { f[decltype(ic)::value].x = fs[decltype(ic)::value]; });
+        }
+        if (m.y & MASK_OTHER) {
+            sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = f[decltype(ic)::value].y; });
+            substitute_is_other_dev<L, WALLS>(g, n1, x0 + 1, y, z, tags.y & PID_MASK, pv, fs);
+            sfor<0, Q>([&](auto ic) { f[decltype(ic)::value].y = fs[decltype(ic)::value]; });
+        }
+    }
+}
+
+// Moving-wall momentum of the bounced values of one site of the pair.
+template <class L, bool WALLS, int H>
+__device__ __forceinline__ void wall_momentum_half(const SweepArgs& a, const Nbr& n, float2 f[])
 {
     constexpr int Q = L::Q;
     float fs[Q];
     sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = half_of<H>(f[decltype(ic)::value]); });
-    if constexpr (PART) {
-        if (*a.pv.pending) {
-            const unsigned m = tagx != TAG_FLUID ? mask : 0u;
-            substitute_is_dev<L, WALLS>(a.g, n, x, y, z, m, tagx & PID_MASK, a.pv, fs);
-        }
-    }
-    if constexpr (WALLS) {
-        if (a.moving_walls && *a.pv.pending) wall_momentum<L, float, WALLS>(n, a.uw->uf, fs);
-    }
+    wall_momentum<L, float, WALLS>(n, a.uw->uf, fs);
     sfor<0, Q>([&](auto ic) { half_of<H>(f[decltype(ic)::value]) = fs[decltype(ic)::value]; });
 }
 
-template <class L, int H>
-__device__ __forceinline__ void bs_half(const SweepArgs& a, int x, int y, int z, unsigned idx, unsigned tagx,
-                                        float2 mrho, float2 mj0, float2 mj1, float2 mj2, float2 f[])
+// BS transfer (Eqs. 5-7) of the BS sites of the pair on packed pairs: the same expression
+// as bs_transfer_dev; each BS site takes f^eq(rho_B, u_p + omega_p x r) and writes its
+// per-site record.
+template <class L>
+__device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int y, int z, unsigned idx, uint2 tags,
+                                                 bool bs0, bool bs1, float2 mrho, float2 mj0, float2 mj1, float2 mj2,
+                                                 float2 f[])
 {
     constexpr int Q = L::Q;
-    float fs[Q];
-    sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = half_of<H>(f[decltype(ic)::value]); });
-    bs_transfer_dev<L>(a, x, y, z, idx, tagx, half_of<H>(mrho), half_of<H>(mj0), half_of<H>(mj1), half_of<H>(mj2),
-                       fs);
-    sfor<0, Q>([&](auto ic) { half_of<H>(f[decltype(ic)::value]) = fs[decltype(ic)::value]; });
+    const unsigned o0 = tags.x & PID_MASK, o1 = tags.y & PID_MASK;
+    const PKernF k0 = a.pv.pkf[bs0 ? o0 : o1];
+    const PKernF k1 = a.pv.pkf[bs1 ? o1 : o0];
+    float2 r[3], u[3], om[3], ub[3];
+    lever_arm2(a.g, k0, k1, x0, y, z, r);
+    kin2(k0, k1, u, om);
+    rigid_velocity2(u, om, r, ub);
+    const float2 rho = add2(mrho, p2(1.0f));
+    const float2 usq15 = mul2(p2(1.5f), fma2(ub[2], ub[2], fma2(ub[1], ub[1], mul2(ub[0], ub[0]))));
+    {
+        const float2 e = mul2(p2((float)L::w(0)), fma2(rho, mul2(usq15, p2(-1.0f)), mrho));
+        if (bs0) f[0].x = e.x;
+        if (bs1) f[0].y = e.y;
+    }
+    sfor<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int j = L::opp(i);
+        if constexpr (j > i) {
+            constexpr float w = (float)L::w(i);
+            const float2 cu = cdot2<L, i>(ub);
+            const float2 even = mul2(p2(w), fma2(rho, fma2(mul2(cu, cu), p2(4.5f), mul2(usq15, p2(-1.0f))), mrho));
+            const float2 odd = mul2(p2(3.0f * w), mul2(rho, cu));
+            const float2 gi = add2(even, odd), gj = sub2(even, odd);
+            if (bs0) {
+                f[i].x = gi.x;
+                f[j].x = gj.x;
+            }
+            if (bs1) {
+                f[i].y = gi.y;
+                f[j].y = gj.y;
+            }
+        }
+    });
+    // dp = rho_B u_B' - (j + F), dl = r x dp (Eqs. 6-7)
+    float2 dv[6];
+    dv[0] = sub2(mul2(rho, ub[0]), add2(mj0, p2(a.F_f[0])));
+    dv[1] = sub2(mul2(rho, ub[1]), add2(mj1, p2(a.F_f[1])));
+    dv[2] = sub2(mul2(rho, ub[2]), add2(mj2, p2(a.F_f[2])));
+    dv[3] = sub2(mul2(r[1], dv[2]), mul2(r[2], dv[1]));
+    dv[4] = sub2(mul2(r[2], dv[0]), mul2(r[0], dv[2]));
+    dv[5] = sub2(mul2(r[0], dv[1]), mul2(r[1], dv[0]));
+    const float sid = __uint_as_float(*a.pv.step_id);
+    float4* sc = (float4*)a.bs_scratch + (size_t)idx * 2;
+    if (bs0) {
+        sc[0] = make_float4(dv[0].x, dv[1].x, dv[2].x, dv[3].x);
+        sc[1] = make_float4(dv[4].x, dv[5].x, __uint_as_float(tags.x), sid);
+    }
+    if (bs1) {
+        sc[2] = make_float4(dv[0].y, dv[1].y, dv[2].y, dv[3].y);
+        sc[3] = make_float4(dv[4].y, dv[5].y, __uint_as_float(tags.y), sid);
+    }
 }
 
 // One block: BX threads along x (2 BX sites) times 128 / BX rows of one z-plane.
@@ -225,17 +394,26 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep2(const SweepArgs a)
     }
     float2 f[Q];
     pull2<L, S, WALLS>((const S*)a.fin, g, n0, n1, x0, y, z, idx, f);
-    if constexpr (PART || WALLS) {
-        particle_pre_half<L, S, WALLS, PART, 0>(a, n0, x0, y, z, tg.x, mk.x, f);
-        particle_pre_half<L, S, WALLS, PART, 1>(a, n1, x0 + 1, y, z, tg.y, mk.y, f);
+    if constexpr (PART) {
+        if (*a.pv.pending) {
+            const uint2 m = make_uint2(tg.x != TAG_FLUID ? mk.x : 0u, tg.y != TAG_FLUID ? mk.y : 0u);
+            substitute_is_dev2<L, WALLS>(g, n0, n1, x0, y, z, m, tg, a.pv, f);
+        }
+    }
+    // A moving wall acts on the bounced value after the IS imposition it may have received.
+    if constexpr (WALLS) {
+        if (a.moving_walls && *a.pv.pending) {
+            wall_momentum_half<L, WALLS, 0>(a, n0, f);
+            wall_momentum_half<L, WALLS, 1>(a, n1, f);
+        }
     }
     float2 mrho, mj0, mj1, mj2;
     collide_dev2<L>(f, a, mrho, mj0, mj1, mj2);
     bool any_is = false;
     bool is0 = false, is1 = false;
     if constexpr (PART) {
-        if (valid && (tg.x >> 30) == CLS_BS) bs_half<L, 0>(a, x0, y, z, idx, tg.x, mrho, mj0, mj1, mj2, f);
-        if (valid && (tg.y >> 30) == CLS_BS) bs_half<L, 1>(a, x0 + 1, y, z, idx + 1, tg.y, mrho, mj0, mj1, mj2, f);
+        const bool bs0 = valid && (tg.x >> 30) == CLS_BS, bs1 = valid && (tg.y >> 30) == CLS_BS;
+        if (bs0 || bs1) bs_transfer_dev2<L>(a, x0, y, z, idx, tg, bs0, bs1, mrho, mj0, mj1, mj2, f);
         is0 = (tg.x >> 30) == CLS_IS;
         is1 = (tg.y >> 30) == CLS_IS;
         any_is = __any_sync(0xFFFFFFFFu, is0 || is1);
