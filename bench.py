@@ -41,7 +41,10 @@ def parse():
     p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="d3q19_512", choices=["d3q19_512", "d2q9_sedimentation", "ensemble_64"])
+    p.add_argument("--workload", default="d3q19_512",
+                   choices=["d3q19_512", "d2q9_sedimentation", "ensemble_64", "closure"])
+    p.add_argument("--closure-cells", type=int, nargs=2, default=[512, 64],
+                   help="closure workload: training and held-out cells (8 spheres each)")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     p.add_argument("--edge", type=int, default=0, help="override the 3D box edge (same solid fraction)")
     p.add_argument("--sweep-shape", type=int, default=-1,
@@ -504,12 +507,89 @@ def run_ensemble(args):
         torch.distributed.destroy_process_group()
 
 
+def run_closure(args):
+    """Learned drag closure: paired coarse (r = 3, 32^3 cells) / fine (r = 12, 128^3 cells)
+    runs of seeded cells with 8 fixed spheres each, the network trained on the GPU on one set
+    of seeds and judged against the fine method on held-out seeds. The value is the drag
+    throughput of coarse + closure expressed as fine-lattice site updates per second (the
+    fine method's work per drag evaluation over the time the closure path takes for it); the
+    fine method's own MLUPS is reported beside it, with the drag errors of both paths."""
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1 and rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_1105_2904_gb300 import build as B
+    from paper_1105_2904_gb300 import closure as CL
+
+    B.build()
+    spec = CL.PairSpec()
+    ntr, nte = args.closure_cells
+    t0 = time.perf_counter()
+    Xtr, Ttr, ctr, ftr, str_ = CL.generate(spec, ntr, seed=1)
+    t_gen = time.perf_counter() - t0
+    Xte, Tte, cte, fte, ste = CL.generate(spec, nte, seed=2)
+    cl = CL.Closure(seed=0)
+    t0 = time.perf_counter()
+    cl.fit(Xtr, Ttr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    e_coarse = CL.drag_errors(cte, fte)
+    e_closure = CL.drag_errors(cl.corrected(Xte, cte, ste), fte)
+    # timing: one batch of held-out cells by each path, CUDA events on the batch stream
+    cells = CL.place(spec, nte, seed=2)
+
+    def timed(fine):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        b = CL._run(spec, cells, fine=fine)
+        ev[1].record()
+        torch.cuda.synchronize()
+        f = spec.factor if fine else 1
+        sites = (spec.L * f) ** 3 * nte * spec.steps * f * f
+        t = ev[0].elapsed_time(ev[1]) / 1e3
+        return b, sites, t
+
+    bc, sites_c, t_c = timed(False)
+    xin = torch.cat([bc.cell(k).closure_features(spec.n_side, spec.spacing, 1e-3) for k in range(nte)], 0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    cl.net.forward(xin)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_inf = ev[0].elapsed_time(ev[1]) / 1e3
+    bc.close()
+    bf, sites_f, t_f = timed(True)
+    bf.close()
+    value = sites_f / (t_c + t_inf) / 1e6
+    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS (fine-lattice equivalent)", "n_gpus": 1,
+            "steps": spec.steps, "warmup": 0, "higher_is_better": True, "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "closure_d3q19_coarse32_r3_fine128_r12", "spheres_per_cell": spec.n_spheres,
+                       "train_samples": int(Xtr.shape[0]), "test_samples": int(Xte.shape[0]),
+                       "network": CL.SIZES, "tau": spec.tau, "coarse_steps": spec.steps},
+            "drag_error_vs_fine": {"coarse_mean": float(e_coarse.mean()), "coarse_p95": float(np.percentile(e_coarse, 95)),
+                                   "closure_mean": float(e_closure.mean()),
+                                   "closure_p95": float(np.percentile(e_closure, 95)),
+                                   "closure_max": float(e_closure.max())},
+            "fine_method": {"value": sites_f / t_f / 1e6, "unit": "MLUPS", "seconds": t_f},
+            "closure_path_seconds": {"coarse_runs": t_c, "inference": t_inf},
+            "speedup_vs_fine_at_drag_accuracy": t_f / (t_c + t_inf),
+            "generation_seconds": t_gen, "training_seconds": t_train}
+    print(json.dumps(line), flush=True)
+    cl.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "ensemble_64":
         run_ensemble(args)
+    elif args.workload == "closure":
+        run_closure(args)
     else:
         run_ours(args)
 

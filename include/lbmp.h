@@ -293,9 +293,11 @@ void lbm_batch_destroy(lbm_batch* b);
 /* Inputs of the learned closure for every particle of ctx, enqueued on the context's stream:
  * the moments (rho - 1, u - u_p) / u_ref at the n_side^3 nodes x_p + spacing (i - (n_side-1)/2,
  * j - .., k - ..), trilinearly interpolated from the 8 surrounding sites of the current state
- * (periodic axes wrap, walled axes clamp to the domain; u as lbm_get_fields). out: device
- * pointer to np * n_side^3 * 4 floats, [p][(k n_side + j) n_side + i][4]. D2Q9: nodes that
- * differ only in k carry the same values.
+ * (periodic axes wrap, walled axes clamp to the domain; u as lbm_get_fields), followed by the
+ * fractional part x_p0 - floor(x_p0) of the particle's reference centre (3 values), which
+ * with the radius fixes the particle's discrete site set. out: device pointer to
+ * np * (4 n_side^3 + 3) floats, [p][(k n_side + j) n_side + i][4] then the 3 offsets. D2Q9:
+ * nodes that differ only in k carry the same values.
  * Errors: LBM_E_INVALID (n_side outside 1..8, spacing <= 0, u_ref zero or not finite). */
 lbm_status lbm_closure_features(lbm_ctx* ctx, int n_side, double spacing, double u_ref, float* out);
 
@@ -318,6 +320,11 @@ long long lbm_mlp_num_params(const lbm_mlp* net);
 
 /* Host FP64 parameters in (rounded to FP32 masters and bfloat16 copies); resets Adam. */
 lbm_status lbm_mlp_set_params(lbm_mlp* net, const double* params);
+
+/* Input standardisation applied by every call that reads inputs (forward, loss, training):
+ * the network sees (x_c - shift[c]) * scale[c] for each of the sizes[0] inputs (host arrays,
+ * copied). Both NULL removes it. Errors: LBM_E_INVALID (one NULL, non-finite entries). */
+lbm_status lbm_mlp_set_input_scaling(lbm_mlp* net, const double* shift, const double* scale);
 
 /* Host copies of the FP32 masters and / or of the last gradients (either may be NULL). */
 lbm_status lbm_mlp_get_params(lbm_mlp* net, double* params, double* grads);

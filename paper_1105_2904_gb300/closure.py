@@ -10,7 +10,15 @@ coarse flow around a sphere, the difference between the fine and the coarse forc
 torque. The coarse method without the network stays the fallback, and the fine method the
 judge of the error.
 
-Everything here is orchestration over the C-ABI: the runs, the stencil moments
+The inputs are the stencil moments (rho - 1, u - u_p) / U on an n_side^3 stencil around the
+particle and the fractional lattice offset of its reference centre, which together with the
+radius fixes the particle's discrete site set (a radius-3 sphere's site count and shape vary
+strongly with it). Inputs are centred on the training set's means and scaled by one common
+spread for all moments (stencil nodes inside the sphere vary little; scaling each to unit
+spread would amplify their noise) and by their own spread for the three offsets; targets
+are standardised per output.
+
+Everything here is orchestration over the C-ABI: the runs, the inputs
 (lbm_closure_features), the training and the inference (lbm_mlp_*) run in the library's
 kernels; torch only holds device memory.
 """
@@ -24,7 +32,8 @@ import numpy as np
 from . import lbmp
 from . import workloads as W
 
-SIZES = [256, 128, 128, 6]
+N_SIDE = 4
+SIZES = [4 * N_SIDE ** 3 + 3, 128, 128, 6]
 
 
 @dataclass
@@ -41,7 +50,7 @@ class PairSpec:
     steps: int = 200
     factor: int = 4
     min_gap: float = 2.0
-    n_side: int = 4
+    n_side: int = N_SIDE
     spacing: float = 4.0     # stencil node spacing (coarse lattice units)
     precision: str = "fp32"
 
@@ -72,7 +81,7 @@ def _run(spec: PairSpec, centers, fine: bool):
 
 
 def generate(spec: PairSpec, n_cells: int, seed: int):
-    """One batch of coarse / fine pairs. Returns (features [N, 256] CUDA tensor,
+    """One batch of coarse / fine pairs. Returns (inputs [N, 4 n_side^3 + 3] CUDA tensor,
     targets [N, 6], coarse [N, 6], fine [N, 6], scale [N, 2]) with N = spheres of all cells;
     force rows are (Fx, Fy, Fz, Tx, Ty, Tz), the fine torque already scaled to coarse units;
     targets are (fine - coarse) divided by the Stokes scales 6 pi nu r U and 6 pi nu r^2 U,
@@ -122,11 +131,17 @@ class Closure:
     def close(self):
         self.net.close()
 
-    def fit(self, X, T, epochs=300, batch=256, lr=1e-3, seed=0):
-        """Trains on features X (CUDA tensor) and targets T (numpy [N, 6]) normalised per
-        output; returns the per-epoch losses."""
+    def fit(self, X, T, epochs=200, batch=128, lr=5e-4, seed=0):
+        """Trains on inputs X (CUDA tensor) and targets T (numpy [N, 6]), scaled with the
+        training set's statistics (module docstring). Returns the per-epoch losses."""
         import torch
 
+        Xh = X.double().cpu().numpy()
+        nm = Xh.shape[1] - 3
+        spread = np.empty(Xh.shape[1])
+        spread[:nm] = Xh[:, :nm].std()
+        spread[nm:] = Xh[:, nm:].std(0)
+        self.net.set_input_scaling(Xh.mean(0), 1.0 / np.where(spread > 0, spread, 1.0))
         self.mu = T.mean(0)
         self.sd = T.std(0) + 1e-12
         Tn = torch.tensor((T - self.mu) / self.sd, dtype=torch.float32, device=X.device)

@@ -195,16 +195,20 @@ __global__ void k_loss_total(const float* __restrict__ partial, int nparts, doub
     loss_out[slot] += s * scale;
 }
 
-// Rows idx[r] of X (FP32, [n][K]) as bfloat16 rows r of Xb, and of T ([n][O]) as rows of Tb.
+// Rows idx[r] of X (FP32, [n][K]) as bfloat16 rows r of Xb, each input standardised as
+// (x - shift[c]) * scale[c] when shift / scale are given, and of T ([n][O]) as rows of Tb.
 __global__ void k_gather(const float* __restrict__ X, const float* __restrict__ T, const int* __restrict__ idx,
-                         int rows, int K, int O, __nv_bfloat16* __restrict__ Xb, float* __restrict__ Tb)
+                         int rows, int K, int O, const float* __restrict__ shift, const float* __restrict__ scale,
+                         __nv_bfloat16* __restrict__ Xb, float* __restrict__ Tb)
 {
     const long long nx = (long long)rows * K, total = nx + (long long)rows * O;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         if (e < nx) {
             const long long r = e / K, c = e % K;
             const long long src = idx ? idx[r] : r;
-            Xb[e] = __float2bfloat16(X[src * K + c]);
+            float v = X[src * K + c];
+            if (shift) v = (v - shift[c]) * scale[c];
+            Xb[e] = __float2bfloat16(v);
         } else if (T) {
             const long long f = e - nx, r = f / O, c = f % O;
             const long long src = idx ? idx[r] : r;
@@ -275,6 +279,8 @@ struct lbm_mlp {
     int idx_cap = 0;
     double* loss_dev = nullptr;
     int loss_cap = 0;
+    float* in_shift = nullptr;       // input standardisation (null: none)
+    float* in_scale = nullptr;
     std::vector<void*> allocs;
     std::string err;
 };
@@ -485,6 +491,32 @@ lbm_status lbm_mlp_set_params(lbm_mlp* net, const double* params)
     return LBM_OK;
 }
 
+lbm_status lbm_mlp_set_input_scaling(lbm_mlp* net, const double* shift, const double* scale)
+{
+    if (!net || (!shift) != (!scale)) return LBM_E_INVALID;
+    const int K = net->sizes[0];
+    if (!shift) {
+        free_dev(net, net->in_shift);
+        free_dev(net, net->in_scale);
+        net->in_shift = net->in_scale = nullptr;
+        return LBM_OK;
+    }
+    std::vector<float> h((size_t)2 * K);
+    for (int c = 0; c < K; ++c) {
+        if (!std::isfinite(shift[c]) || !std::isfinite(scale[c])) return mfail(net, LBM_E_INVALID, "non-finite scaling");
+        h[(size_t)c] = (float)shift[c];
+        h[(size_t)K + c] = (float)scale[c];
+    }
+    lbm_status s = LBM_OK;
+    if (!net->in_shift && ((s = malloc_dev(net, &net->in_shift, (size_t)K)) != LBM_OK ||
+                           (s = malloc_dev(net, &net->in_scale, (size_t)K)) != LBM_OK))
+        return s;
+    MK(cudaMemcpyAsync(net->in_shift, h.data(), sizeof(float) * K, cudaMemcpyHostToDevice, net->stream));
+    MK(cudaMemcpyAsync(net->in_scale, h.data() + K, sizeof(float) * K, cudaMemcpyHostToDevice, net->stream));
+    MK(cudaStreamSynchronize(net->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_mlp_get_params(lbm_mlp* net, double* params, double* grads)
 {
     if (!net || (!params && !grads)) return LBM_E_INVALID;
@@ -509,7 +541,8 @@ lbm_status lbm_mlp_forward(lbm_mlp* net, const float* x, int rows, float* y)
     lbm_status s = ensure_rows(net, rows);
     if (s != LBM_OK) return s;
     const int K = net->sizes[0], O = net->sizes[(size_t)net->L];
-    k_gather<<<blocks_for((long long)rows * K), 256, 0, net->stream>>>(x, nullptr, nullptr, rows, K, O, net->xb, nullptr);
+    k_gather<<<blocks_for((long long)rows * K), 256, 0, net->stream>>>(x, nullptr, nullptr, rows, K, O, net->in_shift,
+                                                                         net->in_scale, net->xb, nullptr);
     forward(net, rows);
     MK(cudaMemcpyAsync(y, net->y, sizeof(float) * (size_t)rows * O, cudaMemcpyDeviceToDevice, net->stream));
     MK(cudaGetLastError());
@@ -524,7 +557,8 @@ lbm_status lbm_mlp_loss_grad(lbm_mlp* net, const float* x, const float* t, int r
     if (s != LBM_OK) return s;
     const int K = net->sizes[0], O = net->sizes[(size_t)net->L];
     MK(cudaMemsetAsync(net->loss_dev, 0, sizeof(double), net->stream));
-    k_gather<<<blocks_for((long long)rows * (K + O)), 256, 0, net->stream>>>(x, t, nullptr, rows, K, O, net->xb, net->tb);
+    k_gather<<<blocks_for((long long)rows * (K + O)), 256, 0, net->stream>>>(x, t, nullptr, rows, K, O, net->in_shift,
+                                                                               net->in_scale, net->xb, net->tb);
     backward(net, rows, 0);
     MK(cudaGetLastError());
     if (loss) {
@@ -567,7 +601,8 @@ lbm_status lbm_mlp_train(lbm_mlp* net, const float* x, const float* t, int n, in
         MK(cudaMemcpyAsync(net->idx, perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, net->stream));
         for (int bi = 0; bi < nb; ++bi) {
             k_gather<<<blocks_for((long long)batch * (K + O)), 256, 0, net->stream>>>(x, t, net->idx + (size_t)bi * batch,
-                                                                                      batch, K, O, net->xb, net->tb);
+                                                                                      batch, K, O, net->in_shift,
+                                                                                      net->in_scale, net->xb, net->tb);
             backward(net, batch, e);
             adam(net, (float)lr, 0.9f, 0.999f, 1e-8f);
         }

@@ -782,13 +782,16 @@ __global__ void k_materialize(const MaterializeArgs a)
 // Closure inputs: for particle p (blockIdx.x) and stencil node q (thread), the moments
 // (rho - 1, u - u_p) / u_ref trilinearly interpolated at x_p + h (i - (n-1)/2, j - ..,
 // k - ..), q = (k n + j) n + i, from the 8 surrounding sites (periodic axes wrap, walled
-// axes clamp to the domain). out[p][q][4].
+// axes clamp to the domain), out[p][q][4]; then the fractional offset phi of the particle's
+// reference centre, out[p][4 n^3 + 0..2].
 template <class L, typename S, bool WALLS>
 __global__ void k_features(const FeatureArgs f)
 {
     const int p = blockIdx.x;
     const int nn = f.n_side * f.n_side * f.n_side;
     const int D = f.m.lattice == 0 ? 2 : 3;
+    const size_t stride = (size_t)nn * 4 + 3;
+    if (threadIdx.x < 3) f.out[(size_t)p * stride + (size_t)nn * 4 + threadIdx.x] = (float)f.pk[p].phi[threadIdx.x];
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
         const int ii[3] = {q % f.n_side, (q / f.n_side) % f.n_side, q / (f.n_side * f.n_side)};
         const Geom& g = f.m.g;
@@ -826,7 +829,7 @@ __global__ void k_features(const FeatureArgs f)
             acc[0] += w * (rho - 1.0);
             for (int k = 0; k < 3; ++k) acc[1 + k] += w * u[k];
         }
-        float* o = f.out + ((size_t)p * nn + q) * 4;
+        float* o = f.out + (size_t)p * stride + (size_t)q * 4;
         o[0] = (float)(acc[0] / f.u_ref);
         for (int k = 0; k < 3; ++k) o[1 + k] = (float)((acc[1 + k] - f.pk[p].u[k]) / f.u_ref);
     }

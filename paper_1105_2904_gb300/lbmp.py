@@ -31,7 +31,8 @@ EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_par
             "lbm_batch_step", "lbm_batch_synchronize", "lbm_batch_profile_steps", "lbm_batch_get_info",
             "lbm_batch_stream", "lbm_schedule_tiles", "lbm_batch_last_error", "lbm_batch_destroy",
             "lbm_closure_features",
-            "lbm_mlp_create", "lbm_mlp_num_params", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_forward",
+            "lbm_mlp_create", "lbm_mlp_num_params", "lbm_mlp_set_params", "lbm_mlp_set_input_scaling",
+            "lbm_mlp_get_params", "lbm_mlp_forward",
             "lbm_mlp_loss_grad", "lbm_mlp_adam_step", "lbm_mlp_train", "lbm_mlp_last_error", "lbm_mlp_destroy")
 # entry points whose return value is not an lbm_status
 _NOT_STATUS = ("lbm_last_error", "lbm_destroy", "lbm_batch_cell", "lbm_batch_stream", "lbm_schedule_tiles",
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_mlp_num_params.restype = ctypes.c_longlong
     lib.lbm_mlp_set_params.argtypes = [P, D]
     lib.lbm_mlp_get_params.argtypes = [P, D, D]
+    lib.lbm_mlp_set_input_scaling.argtypes = [P, D, D]
     lib.lbm_mlp_forward.argtypes = [P, P, i32, P]
     lib.lbm_mlp_loss_grad.argtypes = [P, P, P, i32, D]
     lib.lbm_mlp_adam_step.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -442,9 +444,10 @@ class Simulation:
         lbm_set_sweep_shape(self.h, threads_x)
 
     def closure_features(self, n_side, spacing, u_ref):
-        """Closure inputs of every particle as a CUDA float32 tensor [np, n_side^3 * 4]."""
+        """Closure inputs of every particle as a CUDA float32 tensor [np, 4 n_side^3 + 3]: the
+        stencil moments, then the fractional offset of the reference centre."""
         import torch
-        out = torch.empty((self.np, n_side ** 3 * 4), dtype=torch.float32, device="cuda")
+        out = torch.empty((self.np, 4 * n_side ** 3 + 3), dtype=torch.float32, device="cuda")
         lbm_closure_features(self.h, n_side, spacing, u_ref, out.data_ptr())
         self.synchronize()
         return out
@@ -530,6 +533,15 @@ def lbm_mlp_set_params(h, flat):
     _mcheck(h, load().lbm_mlp_set_params(h, _dp(flat)))
 
 
+def lbm_mlp_set_input_scaling(h, shift, scale):
+    if shift is None:
+        _mcheck(h, load().lbm_mlp_set_input_scaling(h, None, None))
+        return
+    shift = np.ascontiguousarray(shift, dtype=np.float64)
+    scale = np.ascontiguousarray(scale, dtype=np.float64)
+    _mcheck(h, load().lbm_mlp_set_input_scaling(h, _dp(shift), _dp(scale)))
+
+
 def lbm_mlp_get_params(h, params=True, grads=False):
     n = lbm_mlp_num_params(h)
     p = np.empty(n) if params else None
@@ -603,6 +615,10 @@ class MLP:
 
     def set_params(self, layers):
         lbm_mlp_set_params(self.h, pack_params(layers))
+
+    def set_input_scaling(self, shift, scale):
+        """Inputs enter the network as (x - shift) * scale (lbm_mlp_set_input_scaling)."""
+        lbm_mlp_set_input_scaling(self.h, shift, scale)
 
     def params(self):
         p, _ = lbm_mlp_get_params(self.h)

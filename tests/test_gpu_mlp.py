@@ -103,3 +103,27 @@ def test_training_learns_a_smooth_target():
     assert np.all(np.isfinite(losses))
     assert losses[-1] < 0.1 * losses[0]
     net.close()
+
+
+def test_input_scaling_matches_oracle_on_scaled_inputs():
+    # the kernel standardises each input in FP32, (x - shift) * scale, before rounding it to
+    # bfloat16: the oracle sees the same FP32 values
+    sizes = [7, 33, 5]
+    g = np.random.Generator(np.random.PCG64(21))
+    X = (g.normal(3.0, 2.0, (50, 7))).astype(np.float32)
+    shift = g.normal(3.0, 0.5, 7)
+    scale = 1.0 / g.uniform(1.0, 3.0, 7)
+    p = _params(sizes, 13)
+    net = lbmp.MLP(sizes)
+    net.set_params(p)
+    net.set_input_scaling(shift, scale)
+    Y = net.forward(torch.tensor(X, device="cuda")).cpu().double().numpy()
+    Xs = ((X - shift.astype(np.float32)) * scale.astype(np.float32)).astype(np.float64)
+    pf = [[W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)] for W, b in p]
+    Yr, _ = M.forward(pf, Xs, bf16=True)
+    assert _rel(Y, Yr) <= 1e-2
+    net.set_input_scaling(None, None)   # removed: plain inputs again
+    Y0 = net.forward(torch.tensor(X, device="cuda")).cpu().double().numpy()
+    Y0r, _ = M.forward(pf, X.astype(np.float64), bf16=True)
+    assert _rel(Y0, Y0r) <= 1e-2
+    net.close()
