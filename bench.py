@@ -95,7 +95,7 @@ def aggregate_throughput(sites, steps, ms_local):
 
 def source_sha():
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "common.cuh", "kernels.h"):
+    for f in ("sweep.cuh", "sweep2.cuh", "common.cuh", "kernels.h"):
         with open(os.path.join(ROOT, "paper_1105_2904_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -299,11 +299,16 @@ def run_ours(args):
     algo_bytes = bytes_per_site * N
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (prof["sweep_ms"] / 1e3) / 1e9
-    kernel_key = "sweep_%s_%s" % (wl.lattice.lower(), args.precision)
+    # which sweep kernel ran: the two-site one for an explicit two-site shape, or by default for
+    # the 16-bit storages (lbm_set_sweep_shape), where nx is even
+    shape = args.sweep_shape if args.sweep_shape >= 0 else (16 if args.precision in ("fp16", "bf16") else 0)
+    two_site = shape > 0 and args.precision != "fp64" and nx % 2 == 0
+    kernel_key = "%s_%s_%s" % ("sweep2" if two_site else "sweep", wl.lattice.lower(), args.precision)
     rec = traffic_record(kernel_key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (rec["dram_bytes_per_site"] * N if rec else None),
-                "kernel": "k_sweep (fused pull-stream + collide + BS transfer)",
+                "kernel": ("k_sweep2 (two sites per thread, %d threads along x)" % shape if two_site else "k_sweep")
+                          + ": fused pull-stream + IS imposition + collide + BS transfer",
                 "algorithmic_bytes_per_launch": algo_bytes, "sweep_ms": prof["sweep_ms"],
                 "particle_phase_ms": prof["particle_ms"], "step_ms_ungraphed": prof["step_ms"],
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"}
