@@ -500,8 +500,10 @@ def run_ensemble(args):
                        "l2": "inputs larger than L2: %.1f GB of distributions per step" % (algo_bytes / 1e9)},
             "separate_launches": {"value": sep_value, "unit": UNIT, "ms_per_step": sep_ms / args.steps,
                                   "launches_per_step": "one step graph per cell (%d)" % n_cells,
-                                  "error": "same method; each context runs its default (two-site) sweep, "
-                                           "so results agree with the batch to FP32 rounding"},
+                                  "error": ("bitwise identical to the batch (FP32 contexts default to the one-site "
+                                            "sweep, the batch's kernel)" if prec in ("fp32", "fp64") else
+                                            "same method; 16-bit contexts default to the two-site sweep, so results "
+                                            "agree with the batch to storage rounding")},
             "speedup_vs_separate": value / sep_value,
             "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
             "gpu_launches": int(info["launches_per_step"]) * args.steps,
