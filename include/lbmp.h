@@ -177,6 +177,30 @@ lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3]);
  * step graphs. LBM_E_INVALID for other values. */
 lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x);
 
+/* ---- Checkpoint and resume ------------------------------------------------------------------
+ * For long runs that must survive the end of a job (the paper's longest sedimentation runs
+ * take 10^5 steps). A checkpoint holds the state at a step boundary: the distributions the
+ * next step streams (storage format), the owner map and IS-source masks, each particle's
+ * velocities, angular velocities, site-set anchor, position and last force and torque, the
+ * pending-imposition flag and the wall velocities. The constant set-up (lattice, sizes, tau,
+ * forces, faces, particle constants, site templates) is not stored but fingerprinted: a
+ * checkpoint loads only into a context created, configured and given particles by the same
+ * calls with the same arguments (its own steps, if any, are overwritten). The byte layout is
+ * this library build's; it is not a portable file format. */
+
+/* Size in bytes of a checkpoint of ctx. */
+lbm_status lbm_checkpoint_size(lbm_ctx* ctx, unsigned long long* bytes);
+
+/* Copies the state at the current step boundary into buf (host memory, caller-owned, at
+ * least lbm_checkpoint_size bytes). Synchronizes; returns a recorded device error first.
+ * LBM_E_INVALID if bytes is too small. */
+lbm_status lbm_checkpoint_save(lbm_ctx* ctx, void* buf, unsigned long long bytes);
+
+/* Restores a checkpoint written by lbm_checkpoint_save: the next lbm_step continues exactly
+ * (bit for bit) where the saved context stood. Synchronizes. LBM_E_INVALID if buf is not a
+ * checkpoint of this build, is truncated, or was taken from a context set up differently. */
+lbm_status lbm_checkpoint_load(lbm_ctx* ctx, const void* buf, unsigned long long bytes);
+
 /* Largest particle count lbm_bs_exchange_noalloc accepts. */
 #define LBM_NOALLOC_MAX_PARTICLES 65536
 

@@ -26,6 +26,7 @@ LBM_PERIODIC, LBM_NOSLIP = 0, 1
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
             "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_set_sweep_shape", "lbm_bs_exchange_noalloc",
+            "lbm_checkpoint_size", "lbm_checkpoint_save", "lbm_checkpoint_load",
             "lbm_last_error", "lbm_destroy",
             "lbm_batch_create", "lbm_batch_add_particles", "lbm_batch_cell", "lbm_batch_set_tuning",
             "lbm_batch_step", "lbm_batch_synchronize", "lbm_batch_profile_steps", "lbm_batch_get_info",
@@ -75,6 +76,9 @@ def load(path: str = LIB_PATH):
     lib.lbm_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.lbm_profile_steps.argtypes = [P, i32, D]
     lib.lbm_set_sweep_shape.argtypes = [P, i32]
+    lib.lbm_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.lbm_checkpoint_save.argtypes = [P, P, ctypes.c_ulonglong]
+    lib.lbm_checkpoint_load.argtypes = [P, P, ctypes.c_ulonglong]
     lib.lbm_bs_exchange_noalloc.argtypes = [i32, i32, i32, i32, I, D, P, P, i32, P, P, P, P, P, P]
     lib.lbm_last_error.argtypes = [P]
     lib.lbm_last_error.restype = ctypes.c_char_p
@@ -227,6 +231,20 @@ def lbm_profile_steps(h, n):
     out = np.zeros(3)
     _check(h, load().lbm_profile_steps(h, int(n), _dp(out)))
     return {"sweep_ms": float(out[0]), "particle_ms": float(out[1]), "step_ms": float(out[2])}
+
+
+def lbm_checkpoint_save(h):
+    """The context's state at the current step boundary as a numpy uint8 array."""
+    n = ctypes.c_ulonglong()
+    _check(h, load().lbm_checkpoint_size(h, ctypes.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(h, load().lbm_checkpoint_save(h, buf.ctypes.data_as(ctypes.c_void_p), n.value))
+    return buf
+
+
+def lbm_checkpoint_load(h, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(h, load().lbm_checkpoint_load(h, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
 
 
 def lbm_set_sweep_shape(h, threads_x):
@@ -437,6 +455,20 @@ class Simulation:
 
     def profile(self, n):
         return lbm_profile_steps(self.h, n)
+
+    def checkpoint(self):
+        """State at the current step boundary (lbm_checkpoint_save) as a numpy uint8 array."""
+        return lbm_checkpoint_save(self.h)
+
+    def restore(self, buf):
+        """Continues from a checkpoint of a context set up by the same calls."""
+        lbm_checkpoint_load(self.h, buf)
+
+    def save(self, path):
+        self.checkpoint().tofile(path)
+
+    def load(self, path):
+        self.restore(np.fromfile(path, dtype=np.uint8))
 
     def set_sweep_shape(self, threads_x):
         """Sweep kernel shape (lbm_set_sweep_shape): 16, 32, 64, 128 threads along x for the
