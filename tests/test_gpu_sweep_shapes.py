@@ -98,3 +98,53 @@ def test_invalid_shape_is_rejected():
     with pytest.raises(lbmp.LbmError):
         g.set_sweep_shape(48)
     g.close()
+
+
+# D2Q9: settling disks in a closed box (walls on x and y; bounce-back of both sites of a pair at
+# the x walls), the shape of the 1024 x 2048 sedimentation workload at a small size.
+D2_DIMS = (62, 90, 1)
+
+
+@pytest.fixture(scope="module")
+def oracle_2d():
+    c, rad = W.rsa_centers((62, 90), 6, 5.0, seed=81, min_gap=1.0, walls=(1, 1, 0))
+    d = np.full(6, 1.5)
+    r = O.OracleSim(0, *D2_DIMS, 0.7, walls=(1, 1, 0), gravity=(0.0, -2e-3, 0.0), gap=0.5)
+    r.add_particles(c, rad, d)
+    r.step(200)
+    return (c, rad, d), r
+
+
+def _gpu2d(setup, precision, shape):
+    c, rad, d = setup
+    g = lbmp.Simulation(0, *D2_DIMS, 0.7, precision=precision, walls=(1, 1, 0), gravity=(0.0, -2e-3, 0.0), gap=0.5)
+    g.set_sweep_shape(shape)
+    g.add_particles(c, rad, d)
+    g.step(200)
+    return g
+
+
+@pytest.mark.parametrize("shape", [0, 16, 32, 128])
+def test_d2q9_walled_settling_fp32_shapes(shape, oracle_2d):
+    setup, r = oracle_2d
+    g = _gpu2d(setup, "fp32", shape)
+    np.testing.assert_array_equal(g.get_tags(), r.get_tags())
+    rg, ug = g.get_fields()
+    rr, ur = r.get_fields()
+    assert rel(ug, ur) <= 1e-5
+    pg, pr = g.get_particles(), r.get_particles()
+    assert rel(pg["force"], pr["force"]) <= 1e-4
+    assert np.max(np.abs(pg["x"] - pr["x"]) / np.asarray(setup[1])[:, None]) <= 1e-5
+    g.close()
+
+
+@pytest.mark.parametrize("precision,bound", [("fp16", 2e-3), ("bf16", 2e-2)])
+def test_d2q9_walled_settling_reduced_storage_default_shape(precision, bound, oracle_2d):
+    setup, r = oracle_2d
+    g = _gpu2d(setup, precision, -1)
+    rg, ug = g.get_fields()
+    rr, ur = r.get_fields()
+    pg, pr = g.get_particles(), r.get_particles()
+    assert rel(ug, ur) <= bound
+    assert rel(pg["force"], pr["force"]) <= bound
+    g.close()
