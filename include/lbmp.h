@@ -139,6 +139,21 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u);
 lbm_status lbm_get_particles(lbm_ctx* ctx, double* x, double* u, double* omega,
                              double* force, double* torque);
 
+/* Asynchronous form of lbm_get_particles for loops that read the particles every step without
+ * stalling the device: enqueues on the context's stream, after the work enqueued so far, the
+ * packing of x, u, omega, force and torque and their copy into dst, then returns at once.
+ * dst: page-locked host memory (cudaMallocHost, cudaHostRegister, or a pinned torch tensor)
+ * of 15 np + 1 doubles, caller-owned, untouched by the caller until the read-back is waited
+ * for: the five arrays of lbm_get_particles as consecutive [np][3] blocks, then the device
+ * status word. *ticket identifies the read-back. At most 8 may be outstanding.
+ * Errors: LBM_E_INVALID (null argument, no particles, 8 outstanding), LBM_E_CUDA. */
+lbm_status lbm_get_particles_async(lbm_ctx* ctx, double* dst, long long* ticket);
+
+/* Waits until read-back `ticket` has landed in its buffer (work enqueued after it may still
+ * run) and returns the device status it carries (as lbm_synchronize would, for the steps
+ * before it). LBM_E_INVALID for an unknown or already waited ticket. */
+lbm_status lbm_wait_particles(lbm_ctx* ctx, long long ticket);
+
 /* Full distribution state f[Q][N] at the current step boundary (post-propagation, with
  * the IS imposition applied), converted to double. Synchronizes. */
 lbm_status lbm_get_distributions(lbm_ctx* ctx, double* f);

@@ -609,7 +609,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CS(dev_alloc(ctx, &ctx->changed, sizeof(int) * np));
     CS(dev_alloc(ctx, &ctx->restamp, sizeof(int) * np));
     CS(dev_alloc(ctx, &ctx->restamp_flag, sizeof(int) * np));
-    CS(dev_alloc(ctx, &ctx->pout, sizeof(double) * 15 * np));
+    CS(dev_alloc(ctx, &ctx->pout, sizeof(double) * (15 * np + 1)));
     if (!ctx->tag) {
         CS(dev_alloc(ctx, &ctx->tag, sizeof(unsigned) * (size_t)ctx->g.N));
         CS(dev_alloc(ctx, &ctx->dens, (size_t)ctx->kt->compute_bytes * ctx->g.N));
@@ -865,6 +865,47 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, double* x, double* u, double* omega, 
     return LBM_OK;
 }
 
+lbm_status lbm_get_particles_async(lbm_ctx* ctx, double* dst, long long* ticket)
+{
+    if (!ctx || !dst || !ticket) return LBM_E_INVALID;
+    if (ctx->np == 0) return fail(ctx, LBM_E_INVALID, "no particles");
+    int slot = -1;
+    for (int k = 0; k < lbm_ctx::RB_SLOTS; ++k)
+        if (!ctx->rb_busy[k]) {
+            slot = k;
+            break;
+        }
+    if (slot < 0) return fail(ctx, LBM_E_INVALID, "8 particle read-backs are outstanding; wait for one first");
+    if (!ctx->rb_ev[slot]) CK(cudaEventCreateWithFlags(&ctx->rb_ev[slot], cudaEventDisableTiming));
+    const size_t bytes = sizeof(double) * (15 * (size_t)ctx->np + 1);
+    launch_pack_particles(particle_args(ctx), ctx->pout, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dst, ctx->pout, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ctx->rb_ev[slot], ctx->stream));
+    ctx->rb_busy[slot] = true;
+    ctx->rb_dst[slot] = dst;
+    ctx->rb_ticket[slot] = ++ctx->rb_count;
+    *ticket = ctx->rb_count;
+    return LBM_OK;
+}
+
+lbm_status lbm_wait_particles(lbm_ctx* ctx, long long ticket)
+{
+    if (!ctx) return LBM_E_INVALID;
+    for (int k = 0; k < lbm_ctx::RB_SLOTS; ++k) {
+        if (!ctx->rb_busy[k] || ctx->rb_ticket[k] != ticket) continue;
+        ctx->rb_busy[k] = false;
+        CK(cudaEventSynchronize(ctx->rb_ev[k]));
+        const int st = (int)ctx->rb_dst[k][15 * (size_t)ctx->np];
+        if (st == ERR_CAPACITY) return fail(ctx, LBM_E_CAPACITY, "a device work list overflowed (contact pairs)");
+        if (st == ERR_UNSTABLE)
+            return fail(ctx, LBM_E_UNSTABLE, "a particle moved by more than one lattice site in one step");
+        if (st != 0) return fail(ctx, (lbm_status)st, "device status " + std::to_string(st));
+        return LBM_OK;
+    }
+    return fail(ctx, LBM_E_INVALID, "no outstanding particle read-back with this ticket");
+}
+
 lbm_status lbm_get_masks(lbm_ctx* ctx, unsigned* tags)
 {
     if (!ctx || !tags) return LBM_E_INVALID;
@@ -905,6 +946,8 @@ void lbm_destroy(lbm_ctx* ctx)
         if (ctx->gexec[c]) cudaGraphExecDestroy(ctx->gexec[c]);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    for (auto& e : ctx->rb_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -73,7 +73,14 @@ struct lbm_ctx {
     double* staging = nullptr;
     void* pinned = nullptr;  // page-locked host staging for particle read-backs
     size_t pinned_bytes = 0;
-    double* pout = nullptr;  // [15][np] packed particle state on the device
+    double* pout = nullptr;  // [15][np] packed particle state on the device, + the status word
+    // asynchronous particle read-backs (lbm_get_particles_async): a ring of events
+    static constexpr int RB_SLOTS = 8;
+    cudaEvent_t rb_ev[RB_SLOTS] = {};
+    long long rb_ticket[RB_SLOTS] = {};
+    const double* rb_dst[RB_SLOTS] = {};
+    bool rb_busy[RB_SLOTS] = {};
+    long long rb_count = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int launches_per_step = 0;
     long long steps = 0;

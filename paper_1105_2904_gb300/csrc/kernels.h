@@ -202,7 +202,8 @@ int launch_particle_phase_batch_b(const ParticleArgs* cells, const PhaseShape& s
 // After a sweep with moving walls: the current wall velocities become those of the streaming
 // that the next pull completes (wv[0] <- wv[1]), and the pulled values await streaming.
 void launch_wall_advance(WallVel* wv, int* pending, cudaStream_t s);
-// Packs x, u, omega, force, torque of every particle into out (five [np][3] blocks).
+// Packs x, u, omega, force, torque of every particle into out (five [np][3] blocks) and the
+// device status word into out[15 np].
 void launch_pack_particles(const ParticleArgs& a, double* out, cudaStream_t s);
 // Opts the contact kernel into the shared memory its pair list needs.
 cudaError_t prepare_particle_kernels(int pair_cap);

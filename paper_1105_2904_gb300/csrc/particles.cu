@@ -524,12 +524,14 @@ __global__ void k_stamp_all(const ParticleArgs a)
 
 int mark_grid() { return 304; }
 
-// x, u, omega, -dP, -dL of every particle as five [np][3] blocks of out.
+// x, u, omega, -dP, -dL of every particle as five [np][3] blocks of out, then the device
+// status word (as a double) in out[15 np].
 __global__ void k_pack_particles(const ParticleArgs a, double* out)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.np) return;
     const size_t np = (size_t)a.np;
+    if (p == 0) out[15 * np] = (double)*a.status;
+    if (p >= a.np) return;
     for (int k = 0; k < 3; ++k) {
         out[0 * 3 * np + (size_t)p * 3 + k] = a.x[(size_t)p * 3 + k];
         out[1 * 3 * np + (size_t)p * 3 + k] = a.pk[p].u[k];

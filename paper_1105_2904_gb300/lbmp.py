@@ -26,7 +26,8 @@ LBM_PERIODIC, LBM_NOSLIP = 0, 1
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
             "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_set_sweep_shape", "lbm_bs_exchange_noalloc",
-            "lbm_checkpoint_size", "lbm_checkpoint_save", "lbm_checkpoint_load",
+            "lbm_checkpoint_size", "lbm_checkpoint_save", "lbm_checkpoint_load", "lbm_get_particles_async",
+            "lbm_wait_particles",
             "lbm_last_error", "lbm_destroy",
             "lbm_batch_create", "lbm_batch_add_particles", "lbm_batch_cell", "lbm_batch_set_tuning",
             "lbm_batch_step", "lbm_batch_synchronize", "lbm_batch_profile_steps", "lbm_batch_get_info",
@@ -76,6 +77,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.lbm_profile_steps.argtypes = [P, i32, D]
     lib.lbm_set_sweep_shape.argtypes = [P, i32]
+    lib.lbm_get_particles_async.argtypes = [P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lbm_wait_particles.argtypes = [P, ctypes.c_longlong]
     lib.lbm_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
     lib.lbm_checkpoint_save.argtypes = [P, P, ctypes.c_ulonglong]
     lib.lbm_checkpoint_load.argtypes = [P, P, ctypes.c_ulonglong]
@@ -201,6 +204,24 @@ def lbm_get_particles(h, n, out=None):
     _check(h, load().lbm_get_particles(h, _dp(out["x"]), _dp(out["u"]), _dp(out["omega"]),
                                        _dp(out["force"]), _dp(out["torque"])))
     return out
+
+
+def lbm_get_particles_async(h, dst_ptr):
+    """Enqueues a read-back of the particle state into page-locked host memory at dst_ptr
+    (15 np + 1 doubles); returns its ticket."""
+    t = ctypes.c_longlong()
+    _check(h, load().lbm_get_particles_async(h, ctypes.c_void_p(dst_ptr), ctypes.byref(t)))
+    return t.value
+
+
+def lbm_wait_particles(h, ticket):
+    _check(h, load().lbm_wait_particles(h, int(ticket)))
+
+
+def unpack_particles(buf, n):
+    """Views of a read-back buffer (numpy float64, 15 n + 1 values) as the five [n][3] arrays."""
+    keys = ("x", "u", "omega", "force", "torque")
+    return {k: buf[3 * n * i:3 * n * (i + 1)].reshape(n, 3) for i, k in enumerate(keys)}
 
 
 def lbm_get_distributions(h, Q, N, f=None):
@@ -440,6 +461,16 @@ class Simulation:
 
     def get_particles(self):
         return lbm_get_particles(self.h, self.np)
+
+    def get_particles_async(self, pinned):
+        """Enqueues a read-back into `pinned` (a page-locked float64 torch tensor of 15 np + 1
+        values); returns a ticket for wait_particles."""
+        if not (pinned.is_pinned() and str(pinned.dtype) == "torch.float64" and pinned.numel() >= 15 * self.np + 1):
+            raise ValueError("expected a pinned float64 tensor of at least 15 np + 1 values")
+        return lbm_get_particles_async(self.h, pinned.data_ptr())
+
+    def wait_particles(self, ticket):
+        lbm_wait_particles(self.h, ticket)
 
     def get_f(self):
         return lbm_get_distributions(self.h, self.Q, self.N).reshape((self.Q,) + self.shape)
