@@ -194,7 +194,7 @@ lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x);
 
 /* ---- Checkpoint and resume ------------------------------------------------------------------
  * For long runs that must survive the end of a job (the paper's longest sedimentation runs
- * take 10^5 steps). A checkpoint holds the state at a step boundary: the distributions the
+ * take about 10^5 steps). A checkpoint holds the state at a step boundary: the distributions the
  * next step streams (storage format), the owner map and IS-source masks, each particle's
  * velocities, angular velocities, site-set anchor, position and last force and torque, the
  * pending-imposition flag and the wall velocities. The constant set-up (lattice, sizes, tau,

@@ -91,12 +91,13 @@ __global__ void k_reduce_ordered(const ParticleArgs a0, const ParticleArgs* __re
     for (int q = 0; q < 6; ++q) a.acc[(size_t)p * 6 + q] = s[q];
 }
 
-// FP32 modes: one block per particle. Thread t sums entries t, t + T, ... in FP32 (loads
+// FP32 modes: one block of 256 threads per particle (a radius-8 sphere's ~890 BS sites in
+// one round of loads). Thread t sums entries t, t + T, ... in FP32 (loads
 // of four entries in flight), then a fixed tree combines the threads (deterministic), and
 // the total is stored in FP64. Each site's 32-byte record holds the id of the particle that
 // owned it as BS in the sweep and the step it was written in, so no owner-map read is
 // needed.
-constexpr int RT = 128;
+constexpr int RT = 256;
 template <bool B>
 __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
