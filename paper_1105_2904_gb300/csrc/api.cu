@@ -75,8 +75,9 @@ lbm_status ensure_alloc(lbm_ctx* ctx)
 // Classification of the solid sites of one particle around its initial centre (Sec. 2.2,
 // Fig. 2): S = {o : |o - phi|^2 <= r^2} (offsets o from floor(x0)); BS = sites of S with a
 // neighbour (model velocity set) outside S; IS = other sites of S with a neighbour in BS;
-// the rest of S is interior. Entries are emitted in z, y, x lexicographic order.
-void classify(int lattice, const double phi[3], double r, std::vector<int>& out)
+// the rest of S is interior. Entries are emitted grouped BS, IS, interior, each group in
+// z, y, x lexicographic order; n_bs and n_is count the first two groups.
+void classify(int lattice, const double phi[3], double r, std::vector<int>& out, int& n_bs, int& n_is)
 {
     const int D = lattice == 0 ? 2 : 3, Q = lattice == 0 ? 9 : 19;
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -85,47 +86,51 @@ void classify(int lattice, const double phi[3], double r, std::vector<int>& out)
         hi[k] = (int)std::ceil(phi[k] + r) + 1;
     }
     const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
-    auto at = [&](int ox, int oy, int oz) { return ((size_t)(oz - lo[2]) * ey + (oy - lo[1])) * ex + (ox - lo[0]); };
-    std::vector<unsigned char> inS((size_t)ex * ey * ez, 0), cls((size_t)ex * ey * ez, 0);
+    const size_t cells = (size_t)ex * ey * ez;
+    // neighbour i of box cell b is b + off[i] (the box has a one-cell margin around S)
+    long long off[19];
+    for (int i = 0; i < Q; ++i)
+        off[i] = ((long long)lat_c(lattice, i, 2) * ey + lat_c(lattice, i, 1)) * ex + lat_c(lattice, i, 0);
+    std::vector<unsigned char> cls(cells, 0);  // 0 outside S, 1 BS, 2 IS, 3 interior, 4 S unclassified
     const double r2 = r * r;
+    size_t b = 0;
     for (int oz = lo[2]; oz <= hi[2]; ++oz)
         for (int oy = lo[1]; oy <= hi[1]; ++oy)
-            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+            for (int ox = lo[0]; ox <= hi[0]; ++ox, ++b) {
                 const double dx = (double)ox - phi[0];
                 const double dy = (double)oy - phi[1];
                 const double dz = (double)oz - phi[2];
                 const double d2 = dx * dx + dy * dy + dz * dz;
-                inS[at(ox, oy, oz)] = d2 <= r2;
+                cls[b] = d2 <= r2 ? 4 : 0;
             }
-    for (int oz = lo[2]; oz <= hi[2]; ++oz)
-        for (int oy = lo[1]; oy <= hi[1]; ++oy)
-            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-                if (!inS[at(ox, oy, oz)]) continue;
-                for (int i = 1; i < Q; ++i)
-                    if (!inS[at(ox + lat_c(lattice, i, 0), oy + lat_c(lattice, i, 1), oz + lat_c(lattice, i, 2))]) {
-                        cls[at(ox, oy, oz)] = 1;  // BS
-                        break;
-                    }
+    for (size_t c = 0; c < cells; ++c) {
+        if (cls[c] != 4) continue;
+        for (int i = 1; i < Q; ++i)
+            if (cls[c + off[i]] == 0) {
+                cls[c] = 1;  // BS: a neighbour outside S
+                break;
             }
-    for (int oz = lo[2]; oz <= hi[2]; ++oz)
-        for (int oy = lo[1]; oy <= hi[1]; ++oy)
-            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-                const size_t b = at(ox, oy, oz);
-                if (!inS[b] || cls[b] == 1) continue;
-                bool is = false;
-                for (int i = 1; i < Q && !is; ++i)
-                    is = cls[at(ox + lat_c(lattice, i, 0), oy + lat_c(lattice, i, 1), oz + lat_c(lattice, i, 2))] == 1;
-                cls[b] = is ? 2 : 3;
-            }
+    }
+    for (size_t c = 0; c < cells; ++c) {
+        if (cls[c] != 4) continue;
+        bool is = false;
+        for (int i = 1; i < Q && !is; ++i) is = cls[c + off[i]] == 1;
+        cls[c] = is ? 2 : 3;  // IS: a neighbour in BS
+    }
+    // grouped BS, IS, interior; z, y, x lexicographic order inside each group
     out.clear();
-    for (int oz = lo[2]; oz <= hi[2]; ++oz)
-        for (int oy = lo[1]; oy <= hi[1]; ++oy)
-            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-                const size_t b = at(ox, oy, oz);
-                if (!inS[b]) continue;
-                const unsigned c = cls[b] == 1 ? CLS_BS : (cls[b] == 2 ? CLS_IS : CLS_IN);
-                out.push_back(tmpl_pack(ox, oy, oz, c));
-            }
+    n_bs = n_is = 0;
+    for (unsigned char want : {1, 2, 3}) {
+        b = 0;
+        for (int oz = lo[2]; oz <= hi[2]; ++oz)
+            for (int oy = lo[1]; oy <= hi[1]; ++oy)
+                for (int ox = lo[0]; ox <= hi[0]; ++ox, ++b) {
+                    if (cls[b] != want) continue;
+                    out.push_back(tmpl_pack(ox, oy, oz, want == 1 ? CLS_BS : (want == 2 ? CLS_IS : CLS_IN)));
+                }
+        if (want == 1) n_bs = (int)out.size();
+        if (want == 2) n_is = (int)out.size() - n_bs;
+    }
 }
 
 double min_image_h(double d, int n, bool periodic)
@@ -548,28 +553,27 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     }
     // Site classification of each new particle (independent, spread over host threads).
     std::vector<std::vector<int>> tm(n);
+    std::vector<int> nbs(n), nis(n);
     {
         const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
         std::vector<std::thread> th;
         for (unsigned t = 0; t < nt; ++t)
             th.emplace_back([&, t]() {
-                for (int q = (int)t; q < n; q += (int)nt) classify(ctx->lattice, pk[q].phi, pc[q].r, tm[q]);
+                for (int q = (int)t; q < n; q += (int)nt)
+                    classify(ctx->lattice, pk[q].phi, pc[q].r, tm[q], nbs[q], nis[q]);
             });
         for (auto& t : th) t.join();
     }
+    size_t total = ctx->h_tmpl.size();
+    for (int q = 0; q < n; ++q) total += tm[q].size();
+    if (total >= (1ull << 31)) return fail(ctx, LBM_E_INVALID, "too many particle sites");
+    ctx->h_tmpl.reserve(total);
     for (int q = 0; q < n; ++q) {
         pc[q].tmpl_off = (int)ctx->h_tmpl.size();
         pc[q].tmpl_n = (int)tm[q].size();
-        pc[q].n_bs = pc[q].n_is = 0;
-        // grouped BS, IS, interior; lexicographic order kept inside each group
-        for (unsigned want : {CLS_BS, CLS_IS, CLS_IN})
-            for (int e : tm[q])
-                if (tmpl_cls(e) == want) {
-                    ctx->h_tmpl.push_back(e);
-                    if (want == CLS_BS) ++pc[q].n_bs;
-                    if (want == CLS_IS) ++pc[q].n_is;
-                }
-        if (ctx->h_tmpl.size() >= (1ull << 31)) return fail(ctx, LBM_E_INVALID, "too many particle sites");
+        pc[q].n_bs = nbs[q];
+        pc[q].n_is = nis[q];
+        ctx->h_tmpl.insert(ctx->h_tmpl.end(), tm[q].begin(), tm[q].end());
     }
     ctx->h_pc.insert(ctx->h_pc.end(), pc.begin(), pc.end());
     ctx->h_pk.insert(ctx->h_pk.end(), pk.begin(), pk.end());
