@@ -63,6 +63,7 @@ def _lib():
             lib.osim_set_walls.argtypes = [P, I]
             lib.osim_set_particle_options.argtypes = [P, D, ctypes.c_double, ctypes.c_int]
             lib.osim_set_wall_velocity.argtypes = [P, ctypes.c_int, D]
+            lib.osim_set_equilibrium_face.argtypes = [P, ctypes.c_int, D]
             lib.osim_add_particles.argtypes = [P, ctypes.c_int, D, D, D, D, D]
             lib.osim_step.argtypes = [P, ctypes.c_int]
             lib.osim_get_f.argtypes = [P, D]
@@ -95,7 +96,7 @@ class OracleSim:
 
     def __init__(self, lattice, nx, ny, nz, tau, body_force=(0.0, 0.0, 0.0),
                  walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False,
-                 wall_velocity=None):
+                 wall_velocity=None, equilibrium_faces=None):
         self.lib = _lib()
         self.lattice = lattice
         self.Q = 9 if lattice == D2Q9 else 19
@@ -110,6 +111,10 @@ class OracleSim:
             raise ValueError("oracle: walls must be set before particles")
         g = _f64(gravity, (3,))
         self.lib.osim_set_particle_options(self.h, _dp(g), float(gap), int(bool(body_force_on_particles)))
+        for face, u in (equilibrium_faces or {}).items():
+            uu = _f64(u, (3,))
+            if self.lib.osim_set_equilibrium_face(self.h, int(face), _dp(uu)) != 0:
+                raise ValueError("oracle: face %d is not on a walled axis" % face)
         for face, u in (wall_velocity or {}).items():
             self.set_wall_velocity(face, u)
 

@@ -39,6 +39,11 @@
  *   R12 mass and inertia: continuum values of a sphere (3D) or disk (2D).
  *   R15 moving walls (velocity-imposed boundaries of Secs. 3.1-3.2, mechanism not given):
  *      halfway bounce-back with the wall-momentum term -6 w_i (c_i . u_w), density 1.
+ *   R16 equilibrium faces (the paper's own way of imposing a velocity at a site, Sec. 2.2,
+ *      applied to a domain face): moves that leave the domain through such a face bounce
+ *      back (no wall-momentum term); after the collision every fluid site lying on the
+ *      face takes f^eq(rho, u_face), rho its post-collision density. A site on several
+ *      equilibrium faces takes the first of -x, +x, -y, +y, -z, +z.
  *
  * Distribution layout f[i][z][y][x]; lattice velocity order below.
  * Compile with -ffp-contract=off: the arithmetic is meant to be evaluated exactly as written.
@@ -81,6 +86,8 @@ struct osim {
     double tau, omega, F[3];
     int walls[3];
     double wall_u[6][3]; /* velocity of each face (-x,+x,-y,+y,-z,+z); tangential */
+    int eqface[6];       /* 1: equilibrium face (R16) */
+    double eq_u[6][3];   /* velocity imposed on an equilibrium face */
     double g[3], gap;
     int bfp;
     double* f;    /* state at the start of a step (pre-collision), [Q][N] */
@@ -327,9 +334,21 @@ int osim_set_walls(osim* s, const int walls[3])
     return 0;
 }
 
+int osim_set_equilibrium_face(osim* s, int face, const double u[3])
+{
+    if (face < 0 || face > 5 || !s->walls[face / 2]) return -1;
+    s->eqface[face] = 1;
+    for (int k = 0; k < 3; k++) {
+        s->eq_u[face][k] = (s->L.D == 2 && k == 2) ? 0.0 : u[k];
+        s->wall_u[face][k] = 0.0;
+    }
+    return 0;
+}
+
 int osim_set_wall_velocity(osim* s, int face, const double u[3])
 {
     if (face < 0 || face > 5 || !s->walls[face / 2]) return -1;
+    if (s->eqface[face]) return osim_set_equilibrium_face(s, face, u);
     if (u[face / 2] != 0.0) return -2; /* the wall plane does not move along its normal */
     for (int k = 0; k < 3; k++) s->wall_u[face][k] = (s->L.D == 2 && k == 2) ? 0.0 : u[k];
     return 0;
@@ -504,6 +523,23 @@ static void step_once(osim* s)
         for (int i = 0; i < Q; i++) fin[i] = s->f[(long)i * N + x];
         collide(s, fin, fout);
         for (int i = 0; i < Q; i++) s->fp[(long)i * N + x] = fout[i];
+    }
+
+    /* 1b. Equilibrium faces (R16): fluid sites on such a face take f^eq(rho, u_face). */
+    if (s->eqface[0] || s->eqface[1] || s->eqface[2] || s->eqface[3] || s->eqface[4] || s->eqface[5]) {
+        for (int z = 0; z < s->nz; z++)
+            for (int y = 0; y < s->ny; y++)
+                for (int x = 0; x < s->nx; x++) {
+                    const int pos[3] = {x, y, z}, n3[3] = {s->nx, s->ny, s->nz};
+                    int face = -1;
+                    for (int f = 0; f < 6 && face < 0; f++)
+                        if (s->eqface[f] && pos[f / 2] == ((f & 1) ? n3[f / 2] - 1 : 0)) face = f;
+                    const long site = ((long)z * s->ny + y) * s->nx + x;
+                    if (face < 0 || (s->np > 0 && s->tag[site] != TAG_FLUID)) continue;
+                    double rho = 0.0;
+                    for (int i = 0; i < Q; i++) rho += s->fp[(long)i * N + site];
+                    for (int i = 0; i < Q; i++) s->fp[(long)i * N + site] = feq(L, i, rho, s->eq_u[face]);
+                }
     }
 
     /* 2. Particle-fluid momentum transfer at the BS sites (Eqs. 5-9). */

@@ -32,6 +32,11 @@ int osim_set_walls(osim* s, const int walls[3]);
 /* Tangential velocity of a wall face (0..5 = -x,+x,-y,+y,-z,+z); the face must be a wall.
  * Returns 0, or <0 if the face is periodic or u has a normal component. */
 int osim_set_wall_velocity(osim* s, int face, const double u[3]);
+/* Makes a wall face an equilibrium face (R16) imposing velocity u (any direction): fluid
+ * sites on it take f^eq(rho, u) after the collision; moves through it bounce back without a
+ * wall-momentum term. Later osim_set_wall_velocity calls on the face change u. Returns 0, or
+ * <0 if the face is periodic. */
+int osim_set_equilibrium_face(osim* s, int face, const double u[3]);
 /* gravity on particles (net buoyant), contact gap, whether F also acts on particles (F/rho_p). */
 void osim_set_particle_options(osim* s, const double g[3], double gap, int body_force_on_particles);
 

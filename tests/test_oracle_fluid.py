@@ -218,3 +218,48 @@ def test_wall_velocity_must_be_tangential_and_on_a_wall():
         O.OracleSim(O.D2Q9, 8, 8, 1, 0.8, walls=(0, 1, 0), wall_velocity={3: (0.0, 0.01, 0.0)})
     with pytest.raises(ValueError):
         O.OracleSim(O.D2Q9, 8, 8, 1, 0.8, walls=(0, 1, 0), wall_velocity={0: (0.0, 0.01, 0.0)})
+
+
+# ---- Equilibrium faces (reading R16) ------------------------------------------------------
+# A face that imposes a velocity the way the method imposes one at a particle's sites: after
+# the collision its fluid sites take f^eq(rho, u_face); moves out through it bounce back.
+
+
+@pytest.mark.parametrize("lattice,dims", [(O.D2Q9, (6, 20, 1)), (O.D3Q19, (6, 14, 5))])
+def test_equilibrium_faces_keep_a_uniform_tangential_flow(lattice, dims):
+    # f^eq(1, U) with U along the faces: interior sites stay exactly at f^eq(1, U); the face
+    # sites' pre-collision state holds bounced values but is steady.
+    U = 0.02
+    c, w = O.lattice_tables(lattice)
+    nx, ny, nz = dims
+    s = O.OracleSim(lattice, *dims, 0.8, walls=(0, 1, 0), equilibrium_faces={2: (U, 0, 0), 3: (U, 0, 0)})
+    cu = c[:, 0] * U
+    feq = w * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * U * U)
+    f0 = np.broadcast_to(feq[:, None, None, None], (len(w), nz, ny, nx)).copy()
+    s.set_f(f0)
+    s.step(30)
+    f30 = s.get_f()
+    s.step(30)
+    f60 = s.get_f()
+    assert np.max(np.abs(f60 - f30)) <= 1e-15                               # a few ulps
+    assert np.max(np.abs(f60[:, :, 1:-1, :] - f0[:, :, 1:-1, :])) <= 1e-15
+
+
+@pytest.mark.parametrize("lattice,tau", [(O.D2Q9, 0.6), (O.D2Q9, 0.8), (O.D2Q9, 1.3), (O.D3Q19, 0.9)])
+def test_equilibrium_face_couette_profile_closed_form(lattice, tau):
+    # Faces y = 0 and y = ny - 1 at -U and +U. In the steady state the interior profile is
+    # exactly linear. The momentum the first interior site receives from a face site (a pure
+    # equilibrium at -U) equals what a bulk site would send, f^eq(u(0)) minus its post-collision
+    # non-equilibrium part 3 w c_x c_y (tau - 1) du/dy, when u(0) = -U + (tau - 1) du/dy; with
+    # antisymmetry the slope is du/dy = 2U / (ny - 3 + 2 tau) and u(y) = du/dy (y - (ny-1)/2).
+    ny, U = 24, 0.01
+    dims = (4, ny, 1) if lattice == O.D2Q9 else (4, ny, 4)
+    s = O.OracleSim(lattice, *dims, tau, walls=(0, 1, 0), equilibrium_faces={2: (-U, 0, 0), 3: (U, 0, 0)})
+    for _ in range(80):
+        s.step(1000)
+    rho, u = s.get_fields()
+    ux = u[0, :, 0, 0]
+    slope = 2.0 * U / (ny - 3 + 2.0 * tau)
+    y = np.arange(1, ny - 1)
+    want = slope * (y - 0.5 * (ny - 1))
+    assert np.max(np.abs(ux[1:-1] - want)) <= 1e-10 * U
