@@ -66,7 +66,16 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
  *   LBM_BF16DEV : (f_i - w_i)/w_i stored in bfloat16. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2, LBM_BF16DEV = 3 } lbm_precision;
 
-typedef enum { LBM_PERIODIC = 0, LBM_NOSLIP = 1 } lbm_face;
+/* Kinds of domain face. LBM_NOSLIP: halfway bounce-back wall (optionally moving in its own
+ * plane, lbm_set_wall_velocity). LBM_EQUILIBRIUM: imposes a velocity the way the method
+ * imposes one at a particle's sites (Sec. 2.2, Eqs. 5 and 12): after the collision every
+ * fluid site lying on the face takes f^eq(rho, u_face), rho its own post-collision density;
+ * moves that leave the domain through it bounce back (no wall-momentum term). The paper
+ * imposes free-stream velocities on the faces of its drag runs (Sec. 3.1) without stating
+ * the mechanism; this face is the reading that uses the method's own. A site on several
+ * equilibrium faces takes the first of -x, +x, -y, +y, -z, +z; particle sites keep the
+ * particle treatment. */
+typedef enum { LBM_PERIODIC = 0, LBM_NOSLIP = 1, LBM_EQUILIBRIUM = 2 } lbm_face;
 
 /* Creates a simulation of an nx*ny*nz lattice (D2Q9: nz = 1) of BGK fluid with relaxation
  * time tau (viscosity nu = (tau - 1/2)/3, Sec. 2.1 Eq. 4) at rest (f_i = w_i, rho = 1).
@@ -79,7 +88,7 @@ lbm_status lbm_create(lbm_ctx** out, int lattice, int nx, int ny, int nz, double
                       const double body_force[3]);
 
 /* Sets the storage precision (lbm_precision), the kind of each face (lbm_face; order -x,+x,
- * -y,+y,-z,+z; both faces of an axis must agree; NULL = all periodic), the acceleration g of
+ * -y,+y,-z,+z; an axis is periodic on both faces or on neither; NULL = all periodic), the acceleration g of
  * gravity on particles (net buoyant: (1 - 1/rho_p) g, Sec. 3.3-3.4 settling runs; NULL =
  * none), the contact gap added to r_i + r_j in the hard-core trigger (Sec. 2.3), whether F
  * also accelerates particles (F/rho_p), and the CUDA stream (cudaStream_t, may be NULL) on
@@ -92,7 +101,8 @@ lbm_status lbm_configure(lbm_ctx* ctx, int precision, const int faces[6],
                          int body_force_on_particles, void* cuda_stream);
 
 /* Moves wall face `face` (0..5 = -x,+x,-y,+y,-z,+z) in its own plane with velocity u
- * (xyz; u[face/2] must be 0). The paper drives its shear and channel flows through
+ * (xyz; u[face/2] must be 0), or, for an LBM_EQUILIBRIUM face, sets the velocity it imposes
+ * (any direction; it applies from the collision of the next step on). The paper drives its shear and channel flows through
  * velocity-imposed walls (Secs. 3.1-3.2) without stating the mechanism; here a population
  * that bounces off a moving wall gains the wall momentum -6 w_i (c_i . u_w) at reference
  * density 1 (halfway bounce-back). A move crossing two walls takes the wall of its lowest
@@ -102,7 +112,7 @@ lbm_status lbm_configure(lbm_ctx* ctx, int precision, const int faces[6],
  * between steps (the stream is synchronised); lbm_configure clears the velocity of faces it
  * makes periodic.
  * Errors: LBM_E_INVALID (face out of range or periodic, u NULL, not finite, or with a
- * normal component); LBM_E_CUDA. */
+ * normal component on a no-slip face); LBM_E_CUDA. */
 lbm_status lbm_set_wall_velocity(lbm_ctx* ctx, int face, const double u[3]);
 
 /* Adds n rigid spheres (disks for D2Q9) (Sec. 2.2: centre x_p, radius r_p, mass and

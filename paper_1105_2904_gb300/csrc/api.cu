@@ -359,17 +359,23 @@ lbm_status lbm_configure(lbm_ctx* ctx, int precision, const int faces[6], const 
     if (ctx->allocated || ctx->np > 0 || ctx->stepped)
         return fail(ctx, LBM_E_STATE, "lbm_configure must precede particles, distributions and steps");
     if (!table_for(precision)) return fail(ctx, LBM_E_INVALID, "unknown precision");
-    int walls[3] = {0, 0, 0};
+    int walls[3] = {0, 0, 0}, eq = 0;
     if (faces) {
+        for (int f = 0; f < 6; ++f)
+            if (faces[f] != LBM_PERIODIC && faces[f] != LBM_NOSLIP && faces[f] != LBM_EQUILIBRIUM)
+                return fail(ctx, LBM_E_INVALID, "unknown face kind");
         for (int k = 0; k < 3; ++k) {
-            if ((faces[2 * k] != LBM_PERIODIC && faces[2 * k] != LBM_NOSLIP) || faces[2 * k] != faces[2 * k + 1])
-                return fail(ctx, LBM_E_INVALID, "both faces of an axis must be the same kind");
-            walls[k] = faces[2 * k] == LBM_NOSLIP;
+            if ((faces[2 * k] == LBM_PERIODIC) != (faces[2 * k + 1] == LBM_PERIODIC))
+                return fail(ctx, LBM_E_INVALID, "an axis is periodic on both faces or on neither");
+            walls[k] = faces[2 * k] != LBM_PERIODIC;
         }
+        for (int f = 0; f < 6; ++f)
+            if (faces[f] == LBM_EQUILIBRIUM && (ctx->D == 3 || f < 4)) eq |= 1 << f;
     }
     if (ctx->D == 2) walls[2] = 0;
     if (!std::isfinite(contact_gap)) return fail(ctx, LBM_E_INVALID, "contact gap must be finite");
     ctx->precision = precision;
+    ctx->g.eqface = eq;
     for (int k = 0; k < 3; ++k) {
         ctx->g.wall[k] = walls[k];
         ctx->grav[k] = particle_gravity ? particle_gravity[k] : 0.0;
@@ -395,12 +401,13 @@ lbm_status lbm_set_wall_velocity(lbm_ctx* ctx, int face, const double u[3])
     if (!ctx->g.wall[face / 2]) return fail(ctx, LBM_E_INVALID, "the face is periodic, not a wall");
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(u[k])) return fail(ctx, LBM_E_INVALID, "wall velocity must be finite");
-    if (u[face / 2] != 0.0) return fail(ctx, LBM_E_INVALID, "a wall moves only in its own plane");
+    const bool eq_face = (ctx->g.eqface >> face) & 1;
+    if (!eq_face && u[face / 2] != 0.0) return fail(ctx, LBM_E_INVALID, "a wall moves only in its own plane");
     CK(cudaStreamSynchronize(ctx->stream));
     for (int k = 0; k < 3; ++k) ctx->uw[face][k] = (ctx->D == 2 && k == 2) ? 0.0 : u[k];
-    bool moving = false;
+    bool moving = false;  // a moving no-slip wall: the bounce-back gains the wall momentum
     for (int f = 0; f < 6; ++f)
-        for (int k = 0; k < 3; ++k) moving = moving || ctx->uw[f][k] != 0.0;
+        for (int k = 0; k < 3; ++k) moving = moving || (ctx->uw[f][k] != 0.0 && !((ctx->g.eqface >> f) & 1));
     if (ctx->allocated) {
         // Only the current set changes: the streaming still pending (the values the next pull
         // completes) keeps the velocities it was taken with.

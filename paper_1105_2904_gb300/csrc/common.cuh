@@ -172,6 +172,7 @@ struct Geom {
     int nx, ny, nz;
     int wall[3];     // 1 = halfway bounce-back walls on both ends of the axis
     unsigned N;      // number of sites
+    int eqface;      // bit f: face f (-x,+x,-y,+y,-z,+z) imposes its velocity by equilibrium
 };
 
 // Everything the sweep and the getters read of the particle side.

@@ -284,14 +284,14 @@ __device__ __forceinline__ int out_face(const Nbr& n)
 // direction d = opp(i) and returns as f*_d - 6 w_d (c_d . u_w). The same term applies to
 // the deviation g = f - w, since w_i = w_d.
 template <class L, typename C, bool WALLS>
-__device__ __forceinline__ void wall_momentum(const Nbr& n, const C (*__restrict__ uw)[3], C f[])
+__device__ __forceinline__ void wall_momentum(const Nbr& n, int eqface, const C (*__restrict__ uw)[3], C f[])
 {
     if constexpr (WALLS) {
         sfor<0, L::Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr int d = L::opp(i);
             const int face = out_face<L, d>(n);
-            if (face >= 0) {
+            if (face >= 0 && !((eqface >> face) & 1)) {  // equilibrium faces carry no wall term
                 const C cuw = (C)L::c(d, 0) * uw[face][0] + (C)L::c(d, 1) * uw[face][1] +
                               (C)L::c(d, 2) * uw[face][2];
                 f[i] = f[i] - (C)6 * (C)L::w(d) * cuw;
@@ -509,6 +509,19 @@ __global__ void k_update_masks(const MaskArgs a0, const MaskArgs* __restrict__ c
     }
 }
 
+// The equilibrium face site (x, y, z) lies on (the first of -x, +x, -y, +y, -z, +z), or -1.
+__device__ __forceinline__ int eq_face_of(const Geom& g, int x, int y, int z)
+{
+    const int m = g.eqface;
+    if ((m & 1) && x == 0) return 0;
+    if ((m & 2) && x == g.nx - 1) return 1;
+    if ((m & 4) && y == 0) return 2;
+    if ((m & 8) && y == g.ny - 1) return 3;
+    if ((m & 16) && z == 0) return 4;
+    if ((m & 32) && z == g.nz - 1) return 5;
+    return -1;
+}
+
 // BS transfer of one site in the deviation form (Eqs. 5-7): the forced collision keeps the
 // density and adds F to the momentum, so the post-collision rho_B and rho_B u_B are rho and
 // j + F of the pulled values (mrho, mj). The site takes f^eq(rho_B, u_p + omega_p x r) and
@@ -562,9 +575,9 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
     if constexpr (WALLS) {
         if (a.moving_walls && *a.pv.pending) {
             if constexpr (St::deviation)
-                wall_momentum<L, C, WALLS>(n, a.uw->uf, f);
+                wall_momentum<L, C, WALLS>(n, g.eqface, a.uw->uf, f);
             else
-                wall_momentum<L, C, WALLS>(n, a.uw->u, f);
+                wall_momentum<L, C, WALLS>(n, g.eqface, a.uw->u, f);
         }
     }
 
@@ -612,6 +625,27 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
             for (int q = 0; q < 3; ++q) {
                 sc[q] = rhoB * du[q];
                 sc[3 + q] = rhoB * cr[q];
+            }
+        }
+    }
+
+    // Equilibrium faces: a fluid site on one takes f^eq(rho, u_face) of the current face
+    // velocities, rho its post-collision density (the pre-collision one in the deviation
+    // form, equal in exact arithmetic).
+    if constexpr (WALLS) {
+        if (g.eqface) {
+            const int face = eq_face_of(g, x, y, z);
+            if (face >= 0 && (!PART || tagx == TAG_FLUID)) {
+                if constexpr (St::deviation) {
+                    equilibrium_dev<L>(mrho, a.uw[1].uf[face], f);
+                } else {
+                    double rho = 0.0;
+                    sfor<0, Q>([&](auto ic) { rho += f[decltype(ic)::value]; });
+                    sfor<0, Q>([&](auto ic) {
+                        constexpr int i = decltype(ic)::value;
+                        f[i] = feq_plain<L, i>(1.0, rho, a.uw[1].u[face]);
+                    });
+                }
             }
         }
     }
@@ -726,9 +760,9 @@ __device__ __forceinline__ void site_pull(const MaterializeArgs& a, unsigned idx
     if constexpr (WALLS) {
         if (a.moving_walls && *a.pv.pending) {
             if constexpr (St::deviation)
-                wall_momentum<L, C, WALLS>(n, a.uw->uf, f);
+                wall_momentum<L, C, WALLS>(n, g.eqface, a.uw->uf, f);
             else
-                wall_momentum<L, C, WALLS>(n, a.uw->u, f);
+                wall_momentum<L, C, WALLS>(n, g.eqface, a.uw->u, f);
         }
     }
 }

@@ -305,7 +305,17 @@ __device__ __forceinline__ void wall_momentum_half(const SweepArgs& a, const Nbr
     constexpr int Q = L::Q;
     float fs[Q];
     sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = half_of<H>(f[decltype(ic)::value]); });
-    wall_momentum<L, float, WALLS>(n, a.uw->uf, fs);
+    wall_momentum<L, float, WALLS>(n, a.g.eqface, a.uw->uf, fs);
+    sfor<0, Q>([&](auto ic) { half_of<H>(f[decltype(ic)::value]) = fs[decltype(ic)::value]; });
+}
+
+// Equilibrium-face value f^eq(rho, u) of one site of the pair (deviation form).
+template <class L, int H>
+__device__ __forceinline__ void eq_face_half(const float u[3], float drho, float2 f[])
+{
+    constexpr int Q = L::Q;
+    float fs[Q];
+    equilibrium_dev<L>(drho, u, fs);
     sfor<0, Q>([&](auto ic) { half_of<H>(f[decltype(ic)::value]) = fs[decltype(ic)::value]; });
 }
 
@@ -417,6 +427,14 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep2(const SweepArgs a)
         is0 = (tg.x >> 30) == CLS_IS;
         is1 = (tg.y >> 30) == CLS_IS;
         any_is = __any_sync(0xFFFFFFFFu, is0 || is1);
+    }
+    // Equilibrium faces: fluid sites on one take f^eq(rho, u_face) (as the one-site kernel).
+    if constexpr (WALLS) {
+        if (g.eqface) {
+            const int f0 = eq_face_of(g, x0, y, z), f1 = eq_face_of(g, x0 + 1, y, z);
+            if (f0 >= 0 && tg.x == TAG_FLUID) eq_face_half<L, 0>(a.uw[1].uf[f0], mrho.x, f);
+            if (f1 >= 0 && tg.y == TAG_FLUID) eq_face_half<L, 1>(a.uw[1].uf[f1], mrho.y, f);
+        }
     }
     if (!valid) return;
     S* __restrict__ fout = (S*)a.fout;

@@ -21,7 +21,7 @@ STATUS = {0: "LBM_OK", 1: "LBM_E_INVALID", 2: "LBM_E_OOM", 3: "LBM_E_CUDA", 4: "
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16DEV, "bf16": LBM_BF16DEV}
-LBM_PERIODIC, LBM_NOSLIP = 0, 1
+LBM_PERIODIC, LBM_NOSLIP, LBM_EQUILIBRIUM = 0, 1, 2
 
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
@@ -413,16 +413,26 @@ class Simulation:
 
     def __init__(self, lattice, nx, ny, nz, tau, body_force=(0.0, 0.0, 0.0), precision="fp32",
                  walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False,
-                 cuda_stream=None, wall_velocity=None):
+                 cuda_stream=None, wall_velocity=None, equilibrium_faces=None):
+        """walls[k]: no-slip walls at both ends of axis k; equilibrium_faces: {face: velocity}
+        for faces (0..5 = -x,+x,-y,+y,-z,+z) that impose their velocity by equilibrium
+        (LBM_EQUILIBRIUM; their axis is walled); wall_velocity: {face: velocity} of no-slip
+        faces moving in their plane."""
         self.lattice = lattice
         self.Q = 9 if lattice == LBM_D2Q9 else 19
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.h = lbm_create(lattice, nx, ny, nz, tau, body_force)
-        faces = [LBM_NOSLIP if walls[k // 2] else LBM_PERIODIC for k in range(6)]
+        eq = equilibrium_faces or {}
+        faces = []
+        for f in range(6):
+            walled = walls[f // 2] or (2 * (f // 2)) in eq or (2 * (f // 2) + 1) in eq
+            faces.append(LBM_EQUILIBRIUM if f in eq else (LBM_NOSLIP if walled else LBM_PERIODIC))
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         try:
             lbm_configure(self.h, prec, faces, gravity, gap, body_force_on_particles, cuda_stream)
+            for face, u in eq.items():
+                lbm_set_wall_velocity(self.h, face, u)
             for face, u in (wall_velocity or {}).items():
                 lbm_set_wall_velocity(self.h, face, u)
         except Exception:
