@@ -149,8 +149,9 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u);
 lbm_status lbm_get_particles(lbm_ctx* ctx, double* x, double* u, double* omega,
                              double* force, double* torque);
 
-/* Asynchronous form of lbm_get_particles for loops that read the particles every step without
- * stalling the device: enqueues on the context's stream, after the work enqueued so far, the
+/* Asynchronous form of lbm_get_particles (the same quantities, Eqs. 8-9 and 10-13; the
+ * asynchrony has no counterpart in the paper) for loops that read the particles every step
+ * without stalling the device: enqueues on the context's stream, after the work so far, the
  * packing of x, u, omega, force and torque and their copy into dst, then returns at once.
  * dst: page-locked host memory (cudaMallocHost, cudaHostRegister, or a pinned torch tensor)
  * of 15 np + 1 doubles, caller-owned, untouched by the caller until the read-back is waited
@@ -192,7 +193,8 @@ lbm_status lbm_get_info(lbm_ctx* ctx, long long out[6]);
  * synchronizes. Errors as lbm_step; LBM_E_INVALID if n < 1 or out_ms is NULL. */
 lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3]);
 
-/* Shape of the main sweep kernel (a tuning knob; results agree to FP32 rounding). For the
+/* Shape of the main sweep kernel (a tuning knob with no counterpart in the paper, which
+ * describes a serial algorithm; results agree to FP32 rounding). For the
  * FP32 / FP16 / BF16 storages on a lattice with even nx, threads_x = 16, 32, 64 or 128
  * selects the two-site kernel (each thread updates the sites x, x + 1 with paired 8- or
  * 4-byte accesses and packed FP32 pair arithmetic; blocks of 128 threads, threads_x of them
@@ -203,7 +205,7 @@ lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3]);
 lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x);
 
 /* ---- Checkpoint and resume ------------------------------------------------------------------
- * For long runs that must survive the end of a job (the paper's longest sedimentation runs
+ * No counterpart in the paper. For long runs that must survive the end of a job (the paper's longest sedimentation runs
  * take about 10^5 steps). A checkpoint holds the state at a step boundary: the distributions the
  * next step streams (storage format), the owner map and IS-source masks, each particle's
  * velocities, angular velocities, site-set anchor, position and last force and torque, the
