@@ -166,9 +166,12 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(wl, target_s=12.0):
+def cpu_baseline(wl, target_s=12.0, precision=None, shape=-1):
     """The FP64 oracle, as it stands (one host thread), on a bounded sample of the workload:
-    the same suspension scaled to a smaller periodic box with the same solid fraction."""
+    the same suspension scaled to a smaller periodic box with the same solid fraction. With a
+    precision, the CUDA path then runs the same sample for the same steps in that storage and
+    the error of the bench line's configuration against the oracle is returned beside the
+    baseline: (baseline, error)."""
     import oracle as O
 
     edge = 64 if wl.lattice == "D3Q19" else 256
@@ -196,8 +199,29 @@ def cpu_baseline(wl, target_s=12.0):
     t = time.perf_counter()
     sim.step(steps)
     dt = time.perf_counter() - t
-    return {"value": sites * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+    base = {"value": sites * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%s, %d steps, %.1f s, single-threaded FP64 C" % (sample, steps, dt)}
+    if precision is None:
+        return base
+    from paper_1105_2904_gb300 import lbmp
+    if wl.lattice == "D3Q19":
+        g = lbmp.Simulation(1, edge, edge, edge, s.tau, body_force=s.body_force, precision=precision,
+                            body_force_on_particles=s.body_force_on_particles)
+    else:
+        g = lbmp.Simulation(0, edge, 2 * edge, 1, wl.tau, precision=precision, walls=wl.walls, gravity=wl.gravity)
+    g.set_sweep_shape(shape)
+    g.add_particles(c, r, d, v)
+    g.step(1 + steps)
+    _, ug = g.get_fields()
+    pg = g.get_particles()
+    g.close()
+    _, ur = sim.get_fields()
+    pr = sim.get_particles()
+    err = {"velocity": float(np.max(np.abs(ug - ur)) / np.max(np.abs(ur))),
+           "force": float(np.max(np.abs(pg["force"] - pr["force"])) / np.max(np.abs(pr["force"]))),
+           "norm": "max |x - x_oracle| / max |x_oracle| over the field (velocity) or the particles (force)",
+           "sample": "%s, %d steps, same storage and sweep shape as the timed run" % (sample, 1 + steps)}
+    return base, err
 
 
 def run_reference(args):
@@ -352,9 +376,9 @@ def run_ours(args):
                            "followed by a read-back of the particle state to host arrays (asynchronous, "
                            "double-buffered in pinned memory)" % args.steps}
 
-    cpu = None
+    cpu, err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl)
+        cpu, err = cpu_baseline(wl, precision=args.precision, shape=args.sweep_shape)
 
     if rank == 0:
         solid = len(r) * (4.0 / 3.0 * math.pi * wl.radius ** 3) / N if lattice == 1 else None
@@ -370,7 +394,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GB of distributions per step"
                              % (bytes_per_site * N / 1e9)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "error_vs_oracle": err, "e2e": e2e,
             "gpu_launches": int(info["launches_per_step"]) * args.steps,
             "clocks": clk,
         }
