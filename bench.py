@@ -83,14 +83,25 @@ def reduce_max(value):
     return float(t.item())
 
 
-def aggregate_throughput(sites, steps, ms_local):
-    """Whole-job MLUPS of independent replicas: every rank advanced `sites` sites by `steps`
-    steps; the job time is the slowest rank's."""
+def reduce_sum(value):
+    """Sum of a float over all ranks (identity without a process group)."""
+    import torch
     import torch.distributed as dist
 
-    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def aggregate_throughput(sites, steps, ms_local):
+    """Whole-job MLUPS of independent ranks: each rank advanced its own `sites` sites by
+    `steps` steps (replicas of one problem, or distinct cells of an ensemble); the job counts
+    every rank's sites and its time is the slowest rank's."""
     ms = reduce_max(ms_local)
-    return sites * steps * world / (ms / 1e3) / 1e6, ms
+    return reduce_sum(sites) * steps / (ms / 1e3) / 1e6, ms
 
 
 def source_sha():
@@ -421,7 +432,9 @@ def run_ensemble(args):
     from paper_1105_2904_gb300 import lbmp
 
     B.build()
-    e = W.ensemble_cells()
+    # Ensembles shard by cell: every rank advances its own 64 seeded cells (rank 0 the
+    # reference ensemble), with no exchange between ranks.
+    e = W.ensemble_cells(seed=4 + rank)
     n_cells = len(e.dims)
     F = [e.body_force] * n_cells
     prec = args.precision
@@ -519,7 +532,7 @@ def run_ensemble(args):
         dt = reduce_max(dt)
         h2d = sum(c.nbytes + r.nbytes + d.nbytes + v.nbytes
                   for c, r, d, v in zip(e.centers, e.radii, e.densities, e.velocities)) / args.steps
-        e2e = {"value": e.sites * args.steps * world / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": reduce_sum(e.sites) * args.steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(5 * 3 * 8 * e.n_particles),
                "includes": "batch creation, particle upload and site classification, %d steps each followed "
                            "by a particle-state read-back of every cell" % args.steps}
@@ -530,11 +543,11 @@ def run_ensemble(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": e.name, "cells": n_cells, "sites": e.sites, "particles": e.n_particles,
+            "config": {"workload": e.name, "cells": n_cells, "sites": e.sites, "total_cells": n_cells * world, "particles": e.n_particles,
                        "dropped_spheres": int(sum(e.dropped)), "storage": prec,
                        "tuning": {"policy": best["policy"], "order": best["order"], "grid": best["grid"],
                                   "steps_per_graph": spg, "candidates": len(trials)},
-                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "parallelism": ("cells sharded: %d distinct seeded cells per GPU" % n_cells) if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GB of distributions per step" % (algo_bytes / 1e9)},
             "separate_launches": {"value": sep_value, "unit": UNIT, "ms_per_step": sep_ms / args.steps,
                                   "launches_per_step": "one step graph per cell (%d)" % n_cells,
