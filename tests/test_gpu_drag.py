@@ -1,6 +1,9 @@
-"""Hasimoto's square-array drag at resolutions the CPU oracle is too slow for: radius 4, 8 and
-16 (cells of 32^2 to 128^2, up to ~10^5 steps to steady state) on the CUDA path in FP64 storage,
-which reproduces the oracle bit for bit (test_gpu_parity). Pins as in test_oracle_drag."""
+"""Hasimoto's closed forms at resolutions the CPU oracle is too slow for, on the CUDA path in FP64
+storage, which reproduces the oracle bit for bit (test_gpu_parity). 2D: square array of cylinders,
+radius 4, 8, 16 (cells of 32^2 to 128^2, up to ~10^5 steps to steady state), pins as in
+test_oracle_drag. 3D: simple cubic array of spheres, radius 4, 6, 8 in cubes of edge 6 r: the
+offset delta = r - a_eff of the fitted hydrodynamic radius within +-0.15 over the range, and the
+method's own (BS) force below the true drag F L^3."""
 import numpy as np
 import pytest
 
@@ -25,3 +28,50 @@ def test_hasimoto_offset_over_a_fourfold_resolution_range():
     assert np.all((deltas > 0.0) & (deltas < 1.0))
     assert deltas.max() - deltas.min() <= 0.3
     assert np.all((ratios > 0.70) & (ratios < 0.80))
+
+
+def _K3(c):
+    # Hasimoto (1959), simple cubic array of spheres, small solid fraction c:
+    # F / (6 pi mu a U) = 1 / (1 - 1.7601 c^(1/3) + c - 1.5593 c^2 + O(c^(8/3)))
+    return 1.0 - 1.7601 * c ** (1.0 / 3.0) + c - 1.5593 * c * c
+
+
+def steady_sphere(r, tau=1.0, F=1e-6):
+    """A fixed sphere in a periodic cube of edge 6 r (c = 0.019, series truncation ~1e-4) to
+    steady state in FP64 storage; returns (delta = r - a_eff, reported force / (F L^3))."""
+    import math
+    L = int(6 * r)
+    nu = (tau - 0.5) / 3.0
+    s = lbmp.Simulation(1, L, L, L, tau, body_force=(F, 0.0, 0.0), precision="fp64")
+    s.add_particles(np.array([[L / 2 - 0.5] * 3]), [r], [math.inf])
+    prev = None
+    for _ in range(400):
+        s.step(500)
+        Fr = s.get_particles()["force"][0, 0]
+        if prev is not None and abs(Fr - prev) < 1e-7 * abs(Fr):
+            break
+        prev = Fr
+    rho, u = s.get_fields()
+    fluid = s.get_tags() == 0xFFFFFFFF
+    s.close()
+    U = u[..., 0][fluid].sum() / L ** 3
+    Ft = F * L ** 3
+    lo, hi = 0.2 * r, 1.5 * r          # a with Ft / (6 pi nu a U) = 1 / K(c(a)), bisection
+    for _ in range(200):
+        a = 0.5 * (lo + hi)
+        c = 4.0 / 3.0 * math.pi * a ** 3 / L ** 3
+        if Ft / (6.0 * math.pi * nu * a * U) > 1.0 / _K3(c):
+            lo = a
+        else:
+            hi = a
+    return r - a, Fr / Ft
+
+
+def test_hasimoto_sphere_array_offset_is_resolution_independent():
+    res = [steady_sphere(r) for r in (4.0, 6.0, 8.0)]
+    deltas = np.array([d for d, _ in res])
+    ratios = np.array([q for _, q in res])
+    print("3D delta", deltas, "reported / total", ratios)
+    assert np.all((deltas > 0.0) & (deltas < 1.0))
+    assert deltas.max() - deltas.min() <= 0.3
+    assert np.all((ratios > 0.80) & (ratios < 0.95))      # systematically lower (Sec. 3.1)
