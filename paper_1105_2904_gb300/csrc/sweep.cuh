@@ -711,9 +711,21 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep_batch(const BatchSweepA
 {
     using C = typename Store<S>::C;
     constexpr int Q = L::Q;
+    // The tile's cell arguments (~190 bytes) are staged in shared memory by the block and
+    // reloaded only when the cell changes, instead of every thread loading them per tile.
+    __shared__ __align__(16) SweepArgs sa;
+    int cur = -1;
     for (int e = blockIdx.x; e < b.ntiles; e += gridDim.x) {
         const int4 t = b.table[e];
-        const SweepArgs a = b.cells[t.x];
+        if (t.x != cur) {  // block-uniform: one table entry per block and tile
+            __syncthreads();
+            const int* src = reinterpret_cast<const int*>(&b.cells[t.x]);
+            int* dst = reinterpret_cast<int*>(&sa);
+            for (int w = threadIdx.x; w < (int)(sizeof(SweepArgs) / 4); w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+            cur = t.x;
+        }
+        const SweepArgs& a = sa;
         const Geom& g = a.g;
         const int lw = t.z >> 16;
         const int xr = t.y + (int)(threadIdx.x & ((1u << lw) - 1u));
