@@ -213,7 +213,7 @@ lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x);
  * forces, faces, particle constants, site templates) is not stored but fingerprinted: a
  * checkpoint loads only into a context created, configured and given particles by the same
  * calls with the same arguments (its own steps, if any, are overwritten). The byte layout is
- * this library build's; it is not a portable file format. */
+ * this version's of the library, on this machine; it is not a portable file format. */
 
 /* Size in bytes of a checkpoint of ctx. */
 lbm_status lbm_checkpoint_size(lbm_ctx* ctx, unsigned long long* bytes);
@@ -225,7 +225,8 @@ lbm_status lbm_checkpoint_save(lbm_ctx* ctx, void* buf, unsigned long long bytes
 
 /* Restores a checkpoint written by lbm_checkpoint_save: the next lbm_step continues exactly
  * (bit for bit) where the saved context stood. Synchronizes. LBM_E_INVALID if buf is not a
- * checkpoint of this build, is truncated, or was taken from a context set up differently. */
+ * checkpoint written by this version of the library, is truncated, or was taken from a
+ * context set up differently. */
 lbm_status lbm_checkpoint_load(lbm_ctx* ctx, const void* buf, unsigned long long bytes);
 
 /* Largest particle count lbm_bs_exchange_noalloc accepts. */
