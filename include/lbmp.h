@@ -181,8 +181,8 @@ lbm_status lbm_get_masks(lbm_ctx* ctx, unsigned* tags);
 
 /* Introspection: out[0] = number of particles, out[1] = steps taken, out[2] = kernel
  * launches per step in the captured graph, out[3] = device bytes held by the context,
- * out[4] = bytes of distribution storage per site and step moved by the main sweep
- * (2 Q b), out[5] = precision. Returns LBM_E_INVALID if out is NULL. */
+ * out[4] = bytes of distribution storage per site (2 Q b in the pull scheme; Q b plus
+ * two densities with in-place streaming, see lbm_set_streaming), out[5] = precision. Returns LBM_E_INVALID if out is NULL. */
 lbm_status lbm_get_info(lbm_ctx* ctx, long long out[6]);
 
 /* Runs n steps like lbm_step but without graph capture, timing kernel groups with CUDA
@@ -203,6 +203,26 @@ lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3]);
  * FP16 / BF16 storage. FP64 storage always uses the one-site kernel. Drops the captured
  * step graphs. LBM_E_INVALID for other values. */
 lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x);
+
+/* Streaming scheme (no counterpart in the paper, whose Eq. 4 only states that f*_i(x) moves
+ * to x + c_i; results agree bit for bit in FP64 storage):
+ *   LBM_STREAM_PULL (default): two distribution buffers; each sweep gathers f_i(x) from
+ *     x - c_i of the buffer the previous sweep wrote into the other one. 2 Q b bytes of
+ *     distribution storage per site (b = bytes per stored value).
+ *   LBM_STREAM_INPLACE: one buffer, two kinds of sweep taken in turn. The neighbour sweep
+ *     gathers f_i(x) from slot i of x - c_i and writes f*_i(x) into slot opp(i) of x + c_i
+ *     (slot i of x where x + c_i lies beyond a wall); the local sweep reads f_i(x) from slot
+ *     opp(i) of x and writes f*_i(x) into slot i of x. Q b bytes per site plus two arrays of
+ *     one density per site (4 bytes each in FP32 / FP16 / BF16 storage, 8 in FP64) that hold
+ *     the post-collision densities of the IS sites, which keep their populations in this
+ *     scheme. The sweep is always the one-site kernel (lbm_set_sweep_shape is ignored); the
+ *     getters, lbm_set_distributions, the closure inputs and checkpoints see the same state
+ *     as in the pull scheme. Single contexts only (a batch refuses such a cell).
+ * Must be called after lbm_configure and before particles, distributions, steps or anything
+ * that allocates the context's buffers: LBM_E_STATE otherwise; LBM_E_INVALID for an unknown
+ * mode. */
+typedef enum { LBM_STREAM_PULL = 0, LBM_STREAM_INPLACE = 1 } lbm_streaming;
+lbm_status lbm_set_streaming(lbm_ctx* ctx, int mode);
 
 /* ---- Checkpoint and resume ------------------------------------------------------------------
  * No counterpart in the paper. For long runs that must survive the end of a job (the paper's longest sedimentation runs

@@ -49,7 +49,14 @@ lbm_status ensure_alloc(lbm_ctx* ctx)
     const size_t N = ctx->g.N;
     const size_t fbytes = (size_t)ctx->Q * N * (size_t)ctx->kt->elem_bytes;
     CS(dev_alloc(ctx, &ctx->f[0], fbytes));
-    CS(dev_alloc(ctx, &ctx->f[1], fbytes));
+    if (ctx->inplace) {
+        for (int c = 0; c < 2; ++c) {
+            CS(dev_alloc(ctx, &ctx->is_rho[c], (size_t)ctx->kt->compute_bytes * N));
+            CK(cudaMemsetAsync(ctx->is_rho[c], 0, (size_t)ctx->kt->compute_bytes * N, ctx->stream));
+        }
+    } else {
+        CS(dev_alloc(ctx, &ctx->f[1], fbytes));
+    }
     CS(dev_alloc(ctx, &ctx->status, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->pending, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->pending_prev, sizeof(int)));
@@ -229,6 +236,15 @@ SweepArgs sweep_args(lbm_ctx* ctx, int c)
     // automatic shape: measured fastest per storage at the 512^3 suspension (FP32: one-site)
     const bool half = ctx->precision == LBM_FP16DEV || ctx->precision == LBM_BF16DEV;
     a.pair_bx = ctx->sweep_bx < 0 ? (half ? 16 : 0) : ctx->sweep_bx;
+    if (ctx->inplace) {
+        // parity 0: natural layout, neighbour phase next; parity 1: local phase next
+        a.fin = ctx->f[0];
+        a.fout = ctx->f[0];
+        a.aa = 1 + c;
+        a.is_rho_in = ctx->is_rho[c];
+        a.is_rho_out = ctx->is_rho[1 - c];
+        a.pair_bx = 0;
+    }
     return a;
 }
 
@@ -265,11 +281,22 @@ int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
         const ParticleArgs pa = particle_args(ctx);
         const ISFixArgs fa = is_fix_args(ctx, c);
         launches += launch_particle_phase_a(pa, ctx->stream);
-        ctx->kt->is_save(fa, ctx->stream);
-        launches += launch_particle_phase_b(pa, ctx->stream);
-        ctx->kt->is_fix(fa, ctx->stream);
-        ctx->kt->update_masks(mask_args(ctx, true), ctx->stream);
-        launches += 4;
+        if (ctx->inplace) {
+            // in-place streaming: the IS sites kept their populations; only the sites that
+            // became IS need their density in the array the next sweep reads
+            launches += launch_particle_phase_b(pa, ctx->stream);
+            ISFixArgs fi = fa;
+            fi.dens = ctx->is_rho[1 - c];
+            ctx->kt->inplace_fix(fi, ctx->stream);
+            ctx->kt->update_masks(mask_args(ctx, true), ctx->stream);
+            launches += 2;
+        } else {
+            ctx->kt->is_save(fa, ctx->stream);
+            launches += launch_particle_phase_b(pa, ctx->stream);
+            ctx->kt->is_fix(fa, ctx->stream);
+            ctx->kt->update_masks(mask_args(ctx, true), ctx->stream);
+            launches += 4;
+        }
     }
     if (ctx->moving_walls) {
         launch_wall_advance(ctx->wv, ctx->pending, ctx->stream);
@@ -623,7 +650,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CS(dev_alloc(ctx, &ctx->pout, sizeof(double) * (15 * np + 1)));
     if (!ctx->tag) {
         CS(dev_alloc(ctx, &ctx->tag, sizeof(unsigned) * (size_t)ctx->g.N));
-        CS(dev_alloc(ctx, &ctx->dens, (size_t)ctx->kt->compute_bytes * ctx->g.N));
+        if (!ctx->inplace) CS(dev_alloc(ctx, &ctx->dens, (size_t)ctx->kt->compute_bytes * ctx->g.N));
         CS(dev_alloc(ctx, &ctx->cnt, sizeof(Counters)));
         CS(dev_alloc(ctx, &ctx->pairs, sizeof(unsigned long long) * PAIR_CAP));
         CS(dev_alloc(ctx, &ctx->ismask, sizeof(unsigned) * (size_t)ctx->g.N));
@@ -682,6 +709,17 @@ lbm_status lbm_step(lbm_ctx* ctx, int n)
         ctx->cur ^= 1;
         ++ctx->steps;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_streaming(lbm_ctx* ctx, int mode)
+{
+    if (!ctx) return LBM_E_INVALID;
+    if (mode != LBM_STREAM_PULL && mode != LBM_STREAM_INPLACE)
+        return fail(ctx, LBM_E_INVALID, "streaming mode must be LBM_STREAM_PULL or LBM_STREAM_INPLACE");
+    if (ctx->allocated || ctx->np > 0 || ctx->stepped)
+        return fail(ctx, LBM_E_STATE, "lbm_set_streaming must precede particles, distributions and steps");
+    ctx->inplace = mode == LBM_STREAM_INPLACE;
     return LBM_OK;
 }
 
@@ -751,7 +789,9 @@ static lbm_status materialize(lbm_ctx* ctx, int mode, double* out_a, double* out
         MaterializeArgs a{};
         a.lattice = ctx->lattice;
         a.g = ctx->g;
-        a.fin = ctx->f[ctx->cur];
+        a.fin = ctx->f[ctx->inplace ? 0 : ctx->cur];
+        a.aa = ctx->inplace ? ctx->cur : 0;
+        a.is_rho = ctx->inplace ? ctx->is_rho[ctx->cur] : nullptr;
         a.pv = part_view(ctx);
         for (int k = 0; k < 3; ++k) a.F[k] = ctx->F[k];
         wall_args(ctx, a);
@@ -786,7 +826,9 @@ lbm_status lbm_closure_features(lbm_ctx* ctx, int n_side, double spacing, double
     FeatureArgs f{};
     f.m.lattice = ctx->lattice;
     f.m.g = ctx->g;
-    f.m.fin = ctx->f[ctx->cur];
+    f.m.fin = ctx->f[ctx->inplace ? 0 : ctx->cur];
+    f.m.aa = ctx->inplace ? ctx->cur : 0;
+    f.m.is_rho = ctx->inplace ? ctx->is_rho[ctx->cur] : nullptr;
     f.m.pv = part_view(ctx);
     for (int k = 0; k < 3; ++k) f.m.F[k] = ctx->F[k];
     wall_args(ctx, f.m);
@@ -821,7 +863,9 @@ lbm_status lbm_set_distributions(lbm_ctx* ctx, const double* f)
     CS(sync_status(ctx));
     const size_t N = ctx->g.N;
     const size_t chunk = std::min(N, STAGING_BYTES / ((size_t)ctx->Q * sizeof(double)));
-    void* tmp = ctx->f[1 - ctx->cur];
+    // pull scheme: into the other buffer, then shifted so that the pull returns f; in-place
+    // streaming: straight into the layout a neighbour phase leaves (slot opp(i) of x holds f_i(x))
+    void* tmp = ctx->inplace ? ctx->f[0] : ctx->f[1 - ctx->cur];
     for (size_t s0 = 0; s0 < N; s0 += chunk) {
         const size_t cnt = std::min(chunk, N - s0);
         for (int i = 0; i < ctx->Q; ++i)
@@ -834,17 +878,22 @@ lbm_status lbm_set_distributions(lbm_ctx* ctx, const double* f)
         a.dst = tmp;
         a.s0 = (unsigned)s0;
         a.count = (unsigned)cnt;
+        a.opp = ctx->inplace ? 1 : 0;
         ctx->kt->convert_in(a, ctx->stream);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(ctx->stream));
     }
-    UnstreamArgs u{};
-    u.lattice = ctx->lattice;
-    u.g = ctx->g;
-    u.src = tmp;
-    u.dst = ctx->f[ctx->cur];
-    ctx->kt->unstream(u, ctx->stream);
-    CK(cudaGetLastError());
+    if (ctx->inplace) {
+        ctx->cur = 1;
+    } else {
+        UnstreamArgs u{};
+        u.lattice = ctx->lattice;
+        u.g = ctx->g;
+        u.src = tmp;
+        u.dst = ctx->f[ctx->cur];
+        ctx->kt->unstream(u, ctx->stream);
+        CK(cudaGetLastError());
+    }
     CK(cudaMemsetAsync(ctx->pending, 0, sizeof(int), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
@@ -938,7 +987,8 @@ lbm_status lbm_get_info(lbm_ctx* ctx, long long out[6])
     out[1] = ctx->steps;
     out[2] = ctx->launches_per_step;
     out[3] = (long long)ctx->dev_bytes;
-    out[4] = 2LL * ctx->Q * eb;
+    out[4] = ctx->inplace ? (long long)ctx->Q * eb + 2LL * table_for(ctx->precision)->compute_bytes
+                          : 2LL * ctx->Q * eb;
     out[5] = ctx->precision;
     return LBM_OK;
 }

@@ -168,6 +168,7 @@ lbm_status build(lbm_batch* b)
     const int cur = b->cells[0]->cur;
     for (int i = 0; i < nc; ++i) {
         lbm_ctx* ctx = b->cells[(size_t)i];
+        if (ctx->inplace) return bfail(b, LBM_E_STATE, "in-place streaming is for single contexts, not batch cells");
         BS(from_cell(b, i, ensure_alloc(ctx)));
         if (ctx->cur != cur)
             return bfail(b, LBM_E_STATE, "the cells of a batch must share their buffer parity (step them together)");

@@ -3,7 +3,8 @@
 // A checkpoint is the state at a step boundary: the distribution buffer the next sweep reads
 // (in the storage format, IS sites carrying their density), the owner map and the IS-source
 // masks, the particles' kinematic records, positions and last forces, the pending-imposition
-// flag, the step stamp of the boundary-site records and the wall velocities. Everything else
+// flag, the step stamp of the boundary-site records and the wall velocities; with in-place
+// streaming also the layout parity and the IS-site densities the next sweep reads. Everything else
 // a step uses is rebuilt inside the step. The constant part of the set-up (lattice, sizes,
 // tau, forces, faces, particle constants and templates) is not stored: it is fingerprinted,
 // and a checkpoint loads only into a context set up with the same calls.
@@ -18,12 +19,14 @@ using namespace lbmp::host;
 namespace {
 
 constexpr char kMagic[8] = {'L', 'B', 'M', 'P', 'C', 'K', 'P', '1'};
+constexpr int kVersion = 2;
 
 struct CkptHeader {
     char magic[8];
     int version;
     int lattice, nx, ny, nz, precision, Q, elem_bytes, np;
     int moving_walls;
+    int inplace, parity;       // in-place streaming and its layout parity (ctx->cur)
     long long steps;
     unsigned long long fingerprint;
     unsigned long long bytes_total;
@@ -53,6 +56,7 @@ unsigned long long fingerprint(const lbm_ctx* ctx)
     f.val(ctx->g.nz);
     for (int k = 0; k < 3; ++k) f.val(ctx->g.wall[k]);
     f.val(ctx->precision);
+    f.val(ctx->inplace);
     f.val(ctx->tau);
     for (int k = 0; k < 3; ++k) f.val(ctx->F[k]);
     for (int k = 0; k < 3; ++k) f.val(ctx->grav[k]);
@@ -86,7 +90,8 @@ std::vector<Section> sections(lbm_ctx* ctx)
     const size_t N = ctx->g.N;
     const size_t np = (size_t)ctx->np;
     std::vector<Section> s;
-    s.push_back({ctx->f[ctx->cur], (size_t)ctx->Q * N * (size_t)ctx->kt->elem_bytes});
+    s.push_back({ctx->f[ctx->inplace ? 0 : ctx->cur], (size_t)ctx->Q * N * (size_t)ctx->kt->elem_bytes});
+    if (ctx->inplace) s.push_back({ctx->is_rho[ctx->cur], (size_t)ctx->kt->compute_bytes * N});
     if (np > 0) {
         s.push_back({ctx->tag, sizeof(unsigned) * N});
         s.push_back({ctx->ismask, sizeof(unsigned) * N});
@@ -113,7 +118,7 @@ CkptHeader header_of(lbm_ctx* ctx)
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, kMagic, sizeof(kMagic));
-    h.version = 1;
+    h.version = kVersion;
     h.lattice = ctx->lattice;
     h.nx = ctx->g.nx;
     h.ny = ctx->g.ny;
@@ -123,6 +128,8 @@ CkptHeader header_of(lbm_ctx* ctx)
     h.elem_bytes = ctx->kt->elem_bytes;
     h.np = ctx->np;
     h.moving_walls = ctx->moving_walls ? 1 : 0;
+    h.inplace = ctx->inplace ? 1 : 0;
+    h.parity = ctx->cur;
     h.steps = ctx->steps;
     h.fingerprint = fingerprint(ctx);
     h.bytes_total = total_bytes(ctx);
@@ -170,15 +177,20 @@ lbm_status lbm_checkpoint_load(lbm_ctx* ctx, const void* buf, unsigned long long
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
     const CkptHeader mine = header_of(ctx);
-    if (std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.version != 1)
+    if (std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.version != kVersion)
         return fail(ctx, LBM_E_INVALID, "checkpoint: not a checkpoint of this library version");
     if (h.lattice != mine.lattice || h.nx != mine.nx || h.ny != mine.ny || h.nz != mine.nz ||
-        h.precision != mine.precision || h.Q != mine.Q || h.elem_bytes != mine.elem_bytes || h.np != mine.np)
-        return fail(ctx, LBM_E_INVALID, "checkpoint: lattice, sizes, precision or particle count differ");
+        h.precision != mine.precision || h.Q != mine.Q || h.elem_bytes != mine.elem_bytes || h.np != mine.np ||
+        h.inplace != mine.inplace)
+        return fail(ctx, LBM_E_INVALID, "checkpoint: lattice, sizes, precision, streaming or particle count differ");
+    if (h.parity != 0 && h.parity != 1) return fail(ctx, LBM_E_INVALID, "checkpoint: bad layout parity");
     if (h.fingerprint != mine.fingerprint)
         return fail(ctx, LBM_E_INVALID, "checkpoint: the context's set-up (tau, forces, faces, particles) differs");
     if (h.bytes_total != mine.bytes_total || bytes < h.bytes_total)
         return fail(ctx, LBM_E_INVALID, "checkpoint: truncated or inconsistent size");
+    // in-place streaming: the layout (and the density array the next sweep reads) follow the
+    // saved parity
+    if (ctx->inplace) ctx->cur = h.parity;
     const char* p = (const char*)buf + sizeof(h);
     for (const Section& s : sections(ctx)) {
         CK(cudaMemcpy(s.dev, p, s.bytes, cudaMemcpyHostToDevice));

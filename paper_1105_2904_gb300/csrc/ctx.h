@@ -38,7 +38,10 @@ struct lbm_ctx {
     bool allocated = false;
     bool stepped = false;
 
-    void* f[2] = {nullptr, nullptr};
+    void* f[2] = {nullptr, nullptr};  // in-place streaming: f[0] only
+    bool inplace = false;      // lbm_set_streaming(LBM_STREAM_INPLACE); cur = 1 after a neighbour phase
+    void* is_rho[2] = {nullptr, nullptr};  // in-place streaming: [N] compute type, IS-site densities
+                               // (the sweep from parity c reads is_rho[c] and writes is_rho[1 - c])
     void* dens = nullptr;      // [N] compute type: site densities for the IS bookkeeping
     unsigned* tag = nullptr;
     unsigned* ismask = nullptr;

@@ -25,6 +25,14 @@ struct SweepArgs {
     const WallVel* uw;         // wall velocities of the streaming that the pull completes
     int pair_bx;               // deviation storage, even nx: two-site kernel with this many
                                // threads along x (16, 32, 64 or 128); 0: one-site kernel
+    // In-place streaming (fin == fout, one buffer): 0 = the pull scheme above; 1 = the
+    // neighbour phase (site x reads slot i of x - c_i, writes f*_i into slot opp(i) of
+    // x + c_i); 2 = the local phase (site x reads slot opp(i) of x, writes f*_i into slot i).
+    // The IS sites keep their populations; their post-collision densities go to is_rho_out
+    // and the pulls from IS sources read is_rho_in ([N] compute type each).
+    int aa;
+    const void* is_rho_in;
+    void* is_rho_out;
 };
 
 struct MaterializeArgs {
@@ -37,6 +45,9 @@ struct MaterializeArgs {
     const WallVel* uw;
     unsigned s0, count;        // site range [s0, s0 + count)
     int mode;                  // 0: rho[count], u[count][3]; 1: f[Q][count]
+    int aa;                    // 0: pull-source layout; 1: in-place layout after a neighbour
+                               // phase (slot opp(i) of x holds the pulled f_i(x))
+    const void* is_rho;        // in-place streaming: densities of the IS sites ([N] compute type)
     double* out0;
     double* out1;
 };
@@ -47,6 +58,7 @@ struct ConvertArgs {
     const double* f;           // [Q][count] plain distributions
     void* dst;                 // [Q][N] storage format, unshifted
     unsigned s0, count;
+    int opp;                   // 1: f_i goes to slot opp(i) (in-place layout after a neighbour phase)
 };
 
 struct UnstreamArgs {
@@ -126,6 +138,10 @@ struct KernelTable {
     void (*is_fix_batch)(int lattice, const ISFixArgs* cells, int ncells, cudaStream_t);
     void (*update_masks_batch)(int lattice, const MaskArgs* cells, int ncells, cudaStream_t);
     void (*features)(const FeatureArgs&, cudaStream_t);
+    // In-place streaming: after re-marking, the densities of the sites that are now IS
+    // (ISFixArgs.dens = the density array the next sweep reads; s.aa = the layout the sweep
+    // left: 1 after a neighbour phase, 2 after a local phase).
+    void (*inplace_fix)(const ISFixArgs&, cudaStream_t);
     int elem_bytes;
     int compute_bytes;
 };

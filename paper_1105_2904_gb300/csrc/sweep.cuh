@@ -18,6 +18,16 @@
 // pulls from an IS source is then rho_I itself: the imposition needs no second, dependent
 // load. The particle phase keeps this true when site sets move (k_is_density, k_is_restore,
 // k_is_fix).
+//
+// In-place streaming (SweepArgs::aa, one buffer): two kinds of step alternate. From the
+// natural layout (slot i of x holds f*_i(x)) the neighbour phase pulls as above and writes
+// f*_i(x) into slot opp(i) of x + c_i (into slot i of x itself where x + c_i lies beyond a
+// wall, which is the slot the bounced pull of the next step reads); the local phase then
+// finds the pulled f_i(x) in slot opp(i) of x and writes f*_i(x) back into slot i. A site
+// reads and writes the same Q locations in both phases, so no two sites touch one. The
+// sweep's input is gone once it ran, so the density carry (which needs it to restore sites
+// that stop being IS) gives way to a density array: IS sites keep their populations and
+// store rho_I beside them (k_inplace_fix refreshes it for sites that become IS).
 #pragma once
 
 #include <type_traits>
@@ -472,6 +482,28 @@ __device__ __forceinline__ void substitute_is_other_dev(const Geom& g, const Nbr
     }
 }
 
+// In-place streaming: the value pulled in each direction the imposition substitutes (mask
+// bit i, or a source tagged IS of another particle) is replaced by the source's density
+// from the array the previous sweep wrote; the substitution then reads it exactly as it
+// reads a carried density in the pull scheme. Sites with m = 0 have nothing to do.
+template <class L, typename C, bool WALLS>
+__device__ __forceinline__ void is_density_from_array(const Geom& g, const Nbr& n, int x, int y, int z,
+                                                      unsigned idx, unsigned m, const PartView& pv,
+                                                      const C* __restrict__ rho, C f[])
+{
+    if (m == 0) return;
+    sfor<0, L::Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        int sx, sy, sz;
+        unsigned sidx;
+        bool bounce;
+        pull_source<L, i, WALLS>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
+        bool take = ((m >> i) & 1u) != 0;
+        if (!take && (m & MASK_OTHER)) take = (pv.tag[sidx] >> 30) == CLS_IS;
+        if (take) f[i] = rho[sidx];
+    });
+}
+
 // Rebuilds the IS-source masks at the sites of the listed particles (their site sets hold
 // every site whose mask can be non-zero or can have changed).
 template <class L, bool B>
@@ -553,8 +585,9 @@ __device__ __forceinline__ void bs_transfer_dev(const SweepArgs& a, int x, int y
 // the collision, the BS transfer and its per-site record, and the stores (IS sites store
 // their density in every slot). RESTORE: store an IS site's populations instead (the
 // particle phase recomputing a site that stops being IS); the caller may be divergent.
-// Otherwise every lane of the warp calls it (tail lanes with valid = false).
-template <class L, typename S, bool WALLS, bool PART, bool RESTORE = false>
+// Otherwise every lane of the warp calls it (tail lanes with valid = false). AA: the phase
+// of in-place streaming (SweepArgs::aa), whose stores replace the pull scheme's.
+template <class L, typename S, bool WALLS, bool PART, bool RESTORE = false, int AA = 0>
 __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int z, unsigned idx, bool valid,
                                            const Nbr& n, typename Store<S>::C f[], unsigned tagx, unsigned mask)
 {
@@ -565,6 +598,8 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
     if constexpr (PART) {
         if (*a.pv.pending) {
             const unsigned m = tagx != TAG_FLUID ? mask : 0u;
+            if constexpr (AA != 0)
+                is_density_from_array<L, C, WALLS>(g, n, x, y, z, idx, m, a.pv, (const C*)a.is_rho_in, f);
             if constexpr (St::deviation)
                 substitute_is_dev<L, WALLS>(g, n, x, y, z, m, tagx & PID_MASK, a.pv, f);
             else if (m)
@@ -650,8 +685,37 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
         }
     }
 
-    S* __restrict__ fout = (S*)a.fout;
     const size_t N = g.N;
+    if constexpr (AA != 0) {
+        // In-place streaming: populations to the phase's slots; an IS site's density (the sum
+        // of the values as stored, in slot order) to the density array.
+        if (!valid) return;
+        S* out = (S*)a.fout;
+        if constexpr (PART) {
+            if ((tagx >> 30) == CLS_IS) {
+                C dens = (C)0;
+                sfor<0, Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    dens += St::load(St::save(f[i], (C)L::w(i)), (C)L::w(i));
+                });
+                ((C*)a.is_rho_out)[idx] = dens;
+            }
+        }
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            size_t at = (size_t)i * N + idx;
+            if constexpr (AA == 1) {
+                int tx, ty, tz;
+                unsigned tidx;
+                bool beyond;
+                pull_source<L, L::opp(i), WALLS>(g, n, x, y, z, idx, tx, ty, tz, tidx, beyond);
+                if (!beyond) at = (size_t)L::opp(i) * N + tidx;
+            }
+            out[at] = St::save(f[i], (C)L::w(i));
+        });
+        return;
+    }
+    S* __restrict__ fout = (S*)a.fout;
     // IS sites store their post-collision density, the sum of the values as stored, in
     // every slot (density carry); the check is warp-uniform.
     const bool isis = PART && !RESTORE && (tagx >> 30) == CLS_IS;
@@ -701,6 +765,40 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
     C f[Q];
     pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
     sweep_site<L, S, WALLS, PART>(a, x, y, z, idx, valid, n, f, tagx, mask);
+}
+
+// In-place streaming, one phase (PHASE = SweepArgs::aa): the per-site step of k_sweep with
+// the phase's loads and stores on the one buffer (fin == fout).
+template <class L, typename S, bool WALLS, bool PART, int PHASE>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep_inplace(const SweepArgs a)
+{
+    using C = typename Store<S>::C;
+    constexpr int Q = L::Q;
+    const Geom& g = a.g;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const unsigned row = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx;
+    const int xr = blockIdx.x * SWEEP_THREADS + threadIdx.x;
+    const bool valid = xr < g.nx;
+    const int x = valid ? xr : g.nx - 1;
+    const unsigned idx = row + (unsigned)x;
+    const Nbr n = neighbours<WALLS>(g, x, y, z);
+    unsigned tagx = TAG_FLUID, mask = 0;
+    if constexpr (PART) {
+        tagx = a.pv.tag[idx];
+        mask = a.pv.ismask[idx];
+    }
+    C f[Q];
+    if constexpr (PHASE == 1) {
+        pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
+    } else {
+        const S* fin = (const S*)a.fin;
+        const size_t N = g.N;
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            f[i] = Store<S>::load(fin[(size_t)L::opp(i) * N + idx], (C)L::w(i));
+        });
+    }
+    sweep_site<L, S, WALLS, PART, false, PHASE>(a, x, y, z, idx, valid, n, f, tagx, mask);
 }
 
 // One launch over a batch of cells: each block takes tiles of the schedule table (one, or a
@@ -759,10 +857,19 @@ __device__ __forceinline__ void site_pull(const MaterializeArgs& a, unsigned idx
     const int y = (int)((idx / (unsigned)g.nx) % (unsigned)g.ny);
     const int z = (int)(idx / ((unsigned)g.nx * (unsigned)g.ny));
     const Nbr n = neighbours<WALLS>(g, x, y, z);
-    pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
+    if (a.aa == 1) {
+        const S* fin = (const S*)a.fin;
+        sfor<0, L::Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            f[i] = St::load(fin[(size_t)L::opp(i) * g.N + idx], (C)L::w(i));
+        });
+    } else {
+        pull<L, S, WALLS>((const S*)a.fin, g, n, x, y, z, idx, f);
+    }
     if (a.pv.tag != nullptr && a.pv.tag[idx] != TAG_FLUID && *a.pv.pending) {
         const unsigned m = a.pv.ismask[idx];
         if (m) {
+            if (a.is_rho) is_density_from_array<L, C, WALLS>(g, n, x, y, z, idx, m, a.pv, (const C*)a.is_rho, f);
             if constexpr (St::deviation)
                 substitute_is_dev<L, WALLS>(g, n, x, y, z, m, a.pv.tag[idx] & PID_MASK, a.pv, f);
             else
@@ -893,10 +1000,11 @@ __global__ void k_convert_in(const ConvertArgs a)
     sfor<0, L::Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         const double v = a.f[(size_t)i * a.count + t];
+        const size_t at = (size_t)(a.opp ? L::opp(i) : i) * N + a.s0 + t;
         if constexpr (St::deviation)
-            dst[(size_t)i * N + a.s0 + t] = St::save((C)(v - L::w(i)), (C)L::w(i));
+            dst[at] = St::save((C)(v - L::w(i)), (C)L::w(i));
         else
-            dst[(size_t)i * N + a.s0 + t] = St::save((C)v, (C)L::w(i));
+            dst[at] = St::save((C)v, (C)L::w(i));
     });
 }
 
@@ -1056,6 +1164,56 @@ __global__ void k_is_fix(const ISFixArgs a0, const ISFixArgs* __restrict__ cells
     }
 }
 
+// In-place streaming, after re-marking: every visited site that is now IS gets its density
+// in the array the next sweep reads: the sum of its post-collision populations in slot order
+// (the sum the sweep takes), found where the sweep's phase left them (s.aa: 2 = slot i of x;
+// 1 = slot opp(i) of x + c_i, or slot i of x where x + c_i lies beyond a wall).
+template <class L, typename S, bool WALLS>
+__global__ void k_inplace_fix(const ISFixArgs a)
+{
+    using St = Store<S>;
+    using C = typename St::C;
+    if (!a.cnt) return;
+    const int nlist = a.cnt->nchanged;
+    const Geom& g = a.s.g;
+    const size_t N = g.N;
+    const S* fo = (const S*)a.s.fout;
+    C* dens = (C*)a.dens;
+    for (int b = blockIdx.x; b < nlist; b += gridDim.x) {
+        const int p = a.list[b];
+        const PConst pc = a.pc[p];
+        const int Ko[3] = {a.Kold[(size_t)p * 3], a.Kold[(size_t)p * 3 + 1], a.Kold[(size_t)p * 3 + 2]};
+        const int Kn[3] = {a.pk[p].K[0], a.pk[p].K[1], a.pk[p].K[2]};
+        for (int e = threadIdx.x; e < 2 * pc.n_is; e += blockDim.x) {
+            unsigned site;
+            if (!is_entry_site(a, e < pc.n_is ? Ko : Kn, pc.tmpl_off + pc.n_bs + e % pc.n_is, site)) continue;
+            if ((a.s.pv.tag[site] >> 30) != CLS_IS) continue;
+            C d = (C)0;
+            if (a.s.aa == 2) {
+                sfor<0, L::Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    d += St::load(fo[(size_t)i * N + site], (C)L::w(i));
+                });
+            } else {
+                const int x = (int)(site % (unsigned)g.nx);
+                const int y = (int)((site / (unsigned)g.nx) % (unsigned)g.ny);
+                const int z = (int)(site / ((unsigned)g.nx * (unsigned)g.ny));
+                const Nbr n = neighbours<WALLS>(g, x, y, z);
+                sfor<0, L::Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    int tx, ty, tz;
+                    unsigned tidx;
+                    bool beyond;
+                    pull_source<L, L::opp(i), WALLS>(g, n, x, y, z, site, tx, ty, tz, tidx, beyond);
+                    const size_t at = beyond ? (size_t)i * N + site : (size_t)L::opp(i) * N + tidx;
+                    d += St::load(fo[at], (C)L::w(i));
+                });
+            }
+            dens[site] = d;
+        }
+    }
+}
+
 }  // namespace lbmp
 
 #include "sweep2.cuh"
@@ -1078,11 +1236,26 @@ void launch_sweep_v(const SweepArgs& a, cudaStream_t s)
     k_sweep<L, S, WALLS, PART><<<grid, SWEEP_THREADS, 0, s>>>(a);
 }
 
+template <class L, typename S, bool WALLS, bool PART>
+void launch_inplace_v(const SweepArgs& a, cudaStream_t s)
+{
+    const dim3 grid((a.g.nx + SWEEP_THREADS - 1) / SWEEP_THREADS, a.g.ny, a.g.nz);
+    if (a.aa == 1) k_sweep_inplace<L, S, WALLS, PART, 1><<<grid, SWEEP_THREADS, 0, s>>>(a);
+    else k_sweep_inplace<L, S, WALLS, PART, 2><<<grid, SWEEP_THREADS, 0, s>>>(a);
+}
+
 template <class L, typename S>
 void launch_sweep_l(const SweepArgs& a, cudaStream_t s)
 {
     const bool walls = a.g.wall[0] || a.g.wall[1] || a.g.wall[2];
     const bool part = a.pv.tag != nullptr;
+    if (a.aa) {
+        if (walls && part) launch_inplace_v<L, S, true, true>(a, s);
+        else if (walls) launch_inplace_v<L, S, true, false>(a, s);
+        else if (part) launch_inplace_v<L, S, false, true>(a, s);
+        else launch_inplace_v<L, S, false, false>(a, s);
+        return;
+    }
     if (walls && part) launch_sweep_v<L, S, true, true>(a, s);
     else if (walls) launch_sweep_v<L, S, true, false>(a, s);
     else if (part) launch_sweep_v<L, S, false, true>(a, s);
@@ -1172,6 +1345,19 @@ void launch_is_fix(const ISFixArgs& a, cudaStream_t s)
 }
 
 template <typename S>
+void launch_inplace_fix(const ISFixArgs& a, cudaStream_t s)
+{
+    const bool walls = a.s.g.wall[0] || a.s.g.wall[1] || a.s.g.wall[2];
+    if (a.s.lattice == 0) {
+        if (walls) k_inplace_fix<D2Q9, S, true><<<256, 128, 0, s>>>(a);
+        else k_inplace_fix<D2Q9, S, false><<<256, 128, 0, s>>>(a);
+    } else {
+        if (walls) k_inplace_fix<D3Q19, S, true><<<256, 128, 0, s>>>(a);
+        else k_inplace_fix<D3Q19, S, false><<<256, 128, 0, s>>>(a);
+    }
+}
+
+template <typename S>
 void launch_update_masks(const MaskArgs& a, cudaStream_t s)
 {
     if (a.lattice == 0) k_update_masks<D2Q9, false><<<304, 128, 0, s>>>(a, nullptr);
@@ -1243,6 +1429,7 @@ const KernelTable* make_table()
                                   launch_is_fix_batch<S>,
                                   launch_update_masks_batch<S>,
                                   launch_features<S>,
+                                  launch_inplace_fix<S>,
                                   (int)sizeof(S),
                                   (int)sizeof(typename Store<S>::C)};
     return &t;

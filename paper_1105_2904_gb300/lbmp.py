@@ -22,10 +22,13 @@ LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16DEV, "bf16": LBM_BF16DEV}
 LBM_PERIODIC, LBM_NOSLIP, LBM_EQUILIBRIUM = 0, 1, 2
+LBM_STREAM_PULL, LBM_STREAM_INPLACE = 0, 1
+STREAMING = {"pull": LBM_STREAM_PULL, "inplace": LBM_STREAM_INPLACE}
 
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
-            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_set_sweep_shape", "lbm_bs_exchange_noalloc",
+            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_set_sweep_shape", "lbm_set_streaming",
+            "lbm_bs_exchange_noalloc",
             "lbm_checkpoint_size", "lbm_checkpoint_save", "lbm_checkpoint_load", "lbm_get_particles_async",
             "lbm_wait_particles",
             "lbm_last_error", "lbm_destroy",
@@ -77,6 +80,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_get_info.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.lbm_profile_steps.argtypes = [P, i32, D]
     lib.lbm_set_sweep_shape.argtypes = [P, i32]
+    lib.lbm_set_streaming.argtypes = [P, i32]
     lib.lbm_get_particles_async.argtypes = [P, P, ctypes.POINTER(ctypes.c_longlong)]
     lib.lbm_wait_particles.argtypes = [P, ctypes.c_longlong]
     lib.lbm_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
@@ -272,6 +276,10 @@ def lbm_set_sweep_shape(h, threads_x):
     _check(h, load().lbm_set_sweep_shape(h, int(threads_x)))
 
 
+def lbm_set_streaming(h, mode):
+    _check(h, load().lbm_set_streaming(h, int(mode)))
+
+
 def lbm_bs_exchange_noalloc(lattice, nx, ny, nz, walls, body_force, g_ptr, tags_ptr, n, centers_ptr,
                             velocities_ptr, omegas_ptr, force_ptr, torque_ptr, cuda_stream=None):
     """Allocation-free boundary-site momentum exchange on caller-owned device buffers
@@ -413,11 +421,12 @@ class Simulation:
 
     def __init__(self, lattice, nx, ny, nz, tau, body_force=(0.0, 0.0, 0.0), precision="fp32",
                  walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False,
-                 cuda_stream=None, wall_velocity=None, equilibrium_faces=None):
+                 cuda_stream=None, wall_velocity=None, equilibrium_faces=None, streaming="pull"):
         """walls[k]: no-slip walls at both ends of axis k; equilibrium_faces: {face: velocity}
         for faces (0..5 = -x,+x,-y,+y,-z,+z) that impose their velocity by equilibrium
         (LBM_EQUILIBRIUM; their axis is walled); wall_velocity: {face: velocity} of no-slip
-        faces moving in their plane."""
+        faces moving in their plane; streaming: "pull" (two buffers) or "inplace" (one
+        buffer, lbm_set_streaming)."""
         self.lattice = lattice
         self.Q = 9 if lattice == LBM_D2Q9 else 19
         self.shape = (nz, ny, nx)
@@ -431,6 +440,7 @@ class Simulation:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         try:
             lbm_configure(self.h, prec, faces, gravity, gap, body_force_on_particles, cuda_stream)
+            lbm_set_streaming(self.h, STREAMING[streaming] if isinstance(streaming, str) else int(streaming))
             for face, u in eq.items():
                 lbm_set_wall_velocity(self.h, face, u)
             for face, u in (wall_velocity or {}).items():
