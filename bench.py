@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--edge", type=int, default=0, help="override the 3D box edge (same solid fraction)")
     p.add_argument("--sweep-shape", type=int, default=-1,
                    help="sweep kernel shape (lbm_set_sweep_shape): -1 automatic, 0 one-site, 16/32/64/128 two-site")
+    p.add_argument("--streaming", default="pull", choices=["pull", "inplace"],
+                   help="streaming scheme (lbm_set_streaming): pull (two buffers) or inplace (one buffer)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -177,7 +179,7 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(wl, target_s=12.0, precision=None, shape=-1):
+def cpu_baseline(wl, target_s=12.0, precision=None, shape=-1, streaming="pull"):
     """The FP64 oracle, as it stands (one host thread), on a bounded sample of the workload:
     the same suspension scaled to a smaller periodic box with the same solid fraction. With a
     precision, the CUDA path then runs the same sample for the same steps in that storage and
@@ -217,9 +219,10 @@ def cpu_baseline(wl, target_s=12.0, precision=None, shape=-1):
     from paper_1105_2904_gb300 import lbmp
     if wl.lattice == "D3Q19":
         g = lbmp.Simulation(1, edge, edge, edge, s.tau, body_force=s.body_force, precision=precision,
-                            body_force_on_particles=s.body_force_on_particles)
+                            body_force_on_particles=s.body_force_on_particles, streaming=streaming)
     else:
-        g = lbmp.Simulation(0, edge, 2 * edge, 1, wl.tau, precision=precision, walls=wl.walls, gravity=wl.gravity)
+        g = lbmp.Simulation(0, edge, 2 * edge, 1, wl.tau, precision=precision, walls=wl.walls, gravity=wl.gravity,
+                            streaming=streaming)
     g.set_sweep_shape(shape)
     g.add_particles(c, r, d, v)
     g.step(1 + steps)
@@ -231,7 +234,8 @@ def cpu_baseline(wl, target_s=12.0, precision=None, shape=-1):
     err = {"velocity": float(np.max(np.abs(ug - ur)) / np.max(np.abs(ur))),
            "force": float(np.max(np.abs(pg["force"] - pr["force"])) / np.max(np.abs(pr["force"]))),
            "norm": "max |x - x_oracle| / max |x_oracle| over the field (velocity) or the particles (force)",
-           "sample": "%s, %d steps, same storage and sweep shape as the timed run" % (sample, 1 + steps)}
+           "sample": "%s, %d steps, same storage, streaming and sweep shape as the timed run"
+                     % (sample, 1 + steps)}
     return base, err
 
 
@@ -298,7 +302,8 @@ def run_ours(args):
     def make():
         sim = lbmp.Simulation(lattice, nx, ny, nz, wl.tau, body_force=wl.body_force, precision=args.precision,
                               walls=wl.walls, gravity=wl.gravity, gap=0.0,
-                              body_force_on_particles=wl.body_force_on_particles, cuda_stream=stream.cuda_stream)
+                              body_force_on_particles=wl.body_force_on_particles, cuda_stream=stream.cuda_stream,
+                              streaming=args.streaming)
         sim.set_sweep_shape(args.sweep_shape)
         sim.add_particles(c, r, d, v)
         return sim
@@ -329,21 +334,29 @@ def run_ours(args):
     value, ms = aggregate_throughput(N, args.steps, e0.elapsed_time(e1))
 
     # Roofline of the dominant kernel (the sweep): per-launch duration with CUDA events.
-    prof = sim.profile(min(args.steps, 50))
-    bytes_per_site = info["bytes_per_site"]
+    # (an even number of steps: the in-place scheme's two phases in equal numbers)
+    prof = sim.profile(2 * min(args.steps // 2 if args.steps > 1 else 1, 25))
+    # read Q and write Q stored values per site, in either streaming scheme
+    Q = 19 if lattice == 1 else 9
+    bytes_per_site = 2 * Q * {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[args.precision]
     algo_bytes = bytes_per_site * N
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (prof["sweep_ms"] / 1e3) / 1e9
     # which sweep kernel ran: the two-site one for an explicit two-site shape, or by default for
     # the 16-bit storages (lbm_set_sweep_shape), where nx is even
     shape = args.sweep_shape if args.sweep_shape >= 0 else (16 if args.precision in ("fp16", "bf16") else 0)
-    two_site = shape > 0 and args.precision != "fp64" and nx % 2 == 0
-    kernel_key = "%s_%s_%s" % ("sweep2" if two_site else "sweep", wl.lattice.lower(), args.precision)
+    two_site = shape > 0 and args.precision != "fp64" and nx % 2 == 0 and args.streaming == "pull"
+    inplace = args.streaming == "inplace"
+    kernel_key = "%s_%s_%s" % ("sweep_inplace" if inplace else ("sweep2" if two_site else "sweep"),
+                               wl.lattice.lower(), args.precision)
     rec = traffic_record(kernel_key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (rec["dram_bytes_per_site"] * N if rec else None),
-                "kernel": ("k_sweep2 (two sites per thread, %d threads along x)" % shape if two_site else "k_sweep")
-                          + ": fused pull-stream + IS imposition + collide + BS transfer",
+                "kernel": ("k_sweep_inplace (neighbour and local phases in turn, one buffer): fused in-place "
+                           "stream" if inplace else
+                           ("k_sweep2 (two sites per thread, %d threads along x)" % shape if two_site else "k_sweep")
+                           + ": fused pull-stream")
+                          + " + IS imposition + collide + BS transfer",
                 "algorithmic_bytes_per_launch": algo_bytes, "sweep_ms": prof["sweep_ms"],
                 "particle_phase_ms": prof["particle_ms"], "step_ms_ungraphed": prof["step_ms"],
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"}
@@ -389,7 +402,7 @@ def run_ours(args):
 
     cpu, err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, err = cpu_baseline(wl, precision=args.precision, shape=args.sweep_shape)
+        cpu, err = cpu_baseline(wl, precision=args.precision, shape=args.sweep_shape, streaming=args.streaming)
 
     if rank == 0:
         solid = len(r) * (4.0 / 3.0 * math.pi * wl.radius ** 3) / N if lattice == 1 else None
@@ -402,6 +415,8 @@ def run_ours(args):
                        "particles": len(r), "radius": wl.radius, "solid_fraction": solid, "tau": wl.tau,
                        "storage": {"fp32": "fp32 deviations", "fp16": "fp16 scaled deviations",
                                    "bf16": "bf16 scaled deviations", "fp64": "fp64"}[args.precision],
+                       "streaming": args.streaming,
+                       "distribution_bytes": info["bytes_per_site"] * N,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GB of distributions per step"
                              % (bytes_per_site * N / 1e9)},
