@@ -417,6 +417,7 @@ def run_ours(args):
                                    "bf16": "bf16 scaled deviations", "fp64": "fp64"}[args.precision],
                        "streaming": args.streaming,
                        "distribution_bytes": info["bytes_per_site"] * N,
+                       "device_bytes": info["device_bytes"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GB of distributions per step"
                              % (bytes_per_site * N / 1e9)},
