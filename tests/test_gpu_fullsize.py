@@ -7,6 +7,8 @@ on the particle and its near neighbours (the fluid is at rest, so a boundary sit
 populations; at the seeded gaps no contact is predicted). For a seeded sample of particles the
 oracle recomputes that step in a walled sub-box holding the particle and every particle whose
 sites can meet its sites, built from the seeded inputs alone; the CUDA path runs the whole box.
+The 512^3 suspension is checked in both streaming schemes; over 20 steps, the in-place scheme
+must also give every particle the forces, velocities and positions of the pull scheme.
 """
 import numpy as np
 import pytest
@@ -73,8 +75,9 @@ def _compare_tags(sub_tags, near, shift, centre, radius, gpu_tags, wl, D):
     np.testing.assert_array_equal(gpu_tags[zi, gl[1], gl[0]], mapped)
 
 
-@pytest.mark.parametrize("name", ["d3q19_512", "d2q9_sedimentation"])
-def test_full_size_first_step_on_sampled_particles(name):
+@pytest.mark.parametrize("name,streaming", [("d3q19_512", "pull"), ("d3q19_512", "inplace"),
+                                            ("d2q9_sedimentation", "pull")])
+def test_full_size_first_step_on_sampled_particles(name, streaming):
     wl = W.suspension_3d() if name == "d3q19_512" else W.sedimentation_2d()
     D = 3 if wl.lattice == "D3Q19" else 2
     c, r, d, v = wl.particles()
@@ -84,7 +87,7 @@ def test_full_size_first_step_on_sampled_particles(name):
     nx, ny, nz = wl.dims
     sim = lbmp.Simulation(1 if D == 3 else 0, nx, ny, nz, wl.tau, body_force=wl.body_force, precision="fp32",
                           walls=wl.walls, gravity=wl.gravity, gap=0.0,
-                          body_force_on_particles=wl.body_force_on_particles)
+                          body_force_on_particles=wl.body_force_on_particles, streaming=streaming)
     sim.add_particles(c, r, d, v)
     tags_before = sim.get_tags()
     sim.step(1)
@@ -105,3 +108,24 @@ def test_full_size_first_step_on_sampled_particles(name):
         x_ref = ref["x"][0, :D] + shift
         dxp = got["x"][p, :D] - x_ref
         assert np.max(np.abs(dxp)) <= 1e-5 * r[p], p
+
+
+def test_full_size_inplace_streaming_matches_pull():
+    wl = W.suspension_3d()
+    c, r, d, v = wl.particles()
+    nx, ny, nz = wl.dims
+    out = {}
+    for streaming in ("pull", "inplace"):
+        sim = lbmp.Simulation(1, nx, ny, nz, wl.tau, body_force=wl.body_force, precision="fp32", walls=wl.walls,
+                              gravity=wl.gravity, gap=0.0, body_force_on_particles=wl.body_force_on_particles,
+                              streaming=streaming)
+        sim.add_particles(c, r, d, v)
+        sim.step(20)
+        out[streaming] = (sim.get_particles(), sim.get_tags())
+        sim.close()
+    (pp, tp), (pi, ti) = out["pull"], out["inplace"]
+    np.testing.assert_array_equal(ti, tp)
+    for k, tol in (("force", 1e-4), ("torque", 1e-4), ("u", 1e-5)):
+        scale = max(float(np.max(np.abs(pp[k]))), 1e-300)
+        assert float(np.max(np.abs(pi[k] - pp[k]))) <= tol * scale, k
+    assert float(np.max(np.abs(pi["x"] - pp["x"]))) <= 1e-6
