@@ -493,8 +493,10 @@ def run_ensemble(args):
     algo_bytes = bytes_per_site * e.sites
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (prof["sweep_ms"] / 1e3) / 1e9
+    rec = traffic_record("sweep_batch_ensemble_%s" % prec)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_sweep_batch (all cells in one launch)",
+                "traffic": (rec["dram_bytes_per_site"] * e.sites if rec else None),
+                "kernel": "k_sweep_batch (all cells in one launch)",
                 "algorithmic_bytes_per_launch": algo_bytes, "sweep_ms": prof["sweep_ms"],
                 "particle_phase_ms": prof["particle_ms"], "step_ms_ungraphed": prof["step_ms"],
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"}
