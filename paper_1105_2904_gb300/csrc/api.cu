@@ -621,7 +621,12 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     auto release = [&](void* p) {
         if (!p) return;
         auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
-        if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+        if (it != ctx->allocs.end()) {
+            const size_t k = (size_t)(it - ctx->allocs.begin());
+            ctx->dev_bytes -= ctx->alloc_bytes[k];
+            ctx->allocs.erase(it);
+            ctx->alloc_bytes.erase(ctx->alloc_bytes.begin() + (std::ptrdiff_t)k);
+        }
         cudaFree(p);
     };
     for (void* p : {(void*)ctx->pk, (void*)ctx->pkf, (void*)ctx->pk_prev, (void*)ctx->pkf_prev, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->un,

@@ -87,8 +87,9 @@ struct lbm_ctx {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int launches_per_step = 0;
     long long steps = 0;
-    size_t dev_bytes = 0;
+    size_t dev_bytes = 0;            // bytes of the allocations below
     std::vector<void*> allocs;
+    std::vector<size_t> alloc_bytes; // size of allocs[k]
     std::string err;
 };
 
@@ -123,6 +124,7 @@ lbm_status dev_alloc(lbm_ctx* ctx, T** p, size_t bytes)
                                         cudaGetErrorString(e));
     }
     ctx->allocs.push_back(q);
+    ctx->alloc_bytes.push_back(bytes);
     ctx->dev_bytes += bytes;
     *p = (T*)q;
     return LBM_OK;

@@ -1,6 +1,7 @@
 """Asynchronous particle read-back (lbm_get_particles_async / lbm_wait_particles): the same
 values as the synchronous lbm_get_particles, step after step, with read-backs in flight while
-later steps run; the ticket rules."""
+later steps run; the ticket rules. Also the device bytes lbm_get_info reports when particles
+are added in several calls (the arrays of the earlier calls are freed)."""
 import numpy as np
 import pytest
 
@@ -65,3 +66,20 @@ def test_ticket_rules():
     for x in ts[1:] + [t]:
         g.wait_particles(x)
     g.close()
+
+
+def test_device_bytes_after_particles_added_in_two_calls():
+    dims = (40, 34, 30)
+    c, rad = W.rsa_centers(dims, 5, 4.0, seed=91, min_gap=2.0)
+    v = W.gaussian_velocities(5, 0.02, seed=92)
+    one = lbmp.Simulation(1, *dims, 0.7, precision="fp32")
+    one.add_particles(c, rad, np.full(5, 1.5), v)
+    two = lbmp.Simulation(1, *dims, 0.7, precision="fp32")
+    two.add_particles(c[:2], rad[:2], np.full(2, 1.5), v[:2])
+    two.add_particles(c[2:], rad[2:], np.full(3, 1.5), v[2:])
+    assert two.info()["device_bytes"] == one.info()["device_bytes"]
+    one.step(3)
+    two.step(3)
+    np.testing.assert_array_equal(two.get_particles()["force"], one.get_particles()["force"])
+    one.close()
+    two.close()
