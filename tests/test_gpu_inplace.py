@@ -213,3 +213,28 @@ def test_memory_and_restrictions():
     with pytest.raises(lbmp.LbmError):
         bt.step(1)
     bt.close()
+
+
+@pytest.mark.parametrize("lattice,dims", [(0, (61, 47, 1)), (1, (29, 23, 21))], ids=["d2q9_cavity", "d3q19_box"])
+def test_walls_on_every_axis_bit_for_bit(lattice, dims):
+    """Closed box: walls on every axis (at edges a move crosses two walls), a moving
+    lid, a body force and settling particles near the walls."""
+    D = 2 if lattice == 0 else 3
+    walls = (1, 1, 1 if D == 3 else 0)
+
+    def make(streaming):
+        g = lbmp.Simulation(lattice, *dims, 0.75, body_force=(1e-6, 0.0, 0.0), precision="fp64", walls=walls,
+                            gravity=(0.0, -2e-5, 0.0), gap=0.5, streaming=streaming,
+                            wall_velocity={3: (0.02, 0.0, 0.0)})
+        c, rad = W.rsa_centers(dims if D == 3 else dims[:2], 3, 4.0, seed=17, min_gap=1.5, walls=walls)
+        v = W.gaussian_velocities(3, 0.01, seed=18, dims=D)
+        g.add_particles(c, rad, np.array([1.5, 2.0, 1.2]), v)
+        return g
+
+    a, b = make("inplace"), make("pull")
+    for n in (1, 24, 25):
+        a.step(n)
+        b.step(n)
+        assert_same(state(a), state(b))
+    a.close()
+    b.close()
