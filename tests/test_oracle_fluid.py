@@ -73,6 +73,30 @@ def test_golden_viscosity_of_tau_0_6():
     assert abs(nu_measured - g["nu"]) / g["nu"] < 1e-9
 
 
+def test_golden_504_disk_case_reads_as_a_2_cm_box():
+    # Sec. 3.4 prints 512 x 512 sites, tau = 0.9915, a 0.00025 s time step and nu = 1e-6 m^2/s.
+    # Through nu_phys = nu_lattice dx^2 / dt with the oracle's measured lattice viscosity at that
+    # tau they fix dx = 39.06 um: the 512 sites span 2 cm, not the printed 1e-2 m (reading R17).
+    # The printed diameter 0.625 cm would then be 160 sites and 504 such disks would cover the
+    # box 38 times over; 0.0625 cm = 16 sites covers 39 % of it.
+    g = json.load(open(GOLDEN))["sedimentation_504"]
+    F, ny = 1e-6, 16
+    _, ux = _channel(O.D2Q9, g["tau"], F, ny, 40000)
+    nu_l = -F / np.mean(ux[2:] - 2.0 * ux[1:-1] + ux[:-2])
+    dx = math.sqrt(g["nu_m2_s"] * g["dt_s"] / nu_l)
+    assert abs(g["sites"] * dx - 0.02) / 0.02 < 2e-3
+    assert abs(g["sites"] * dx - g["box_printed_m"]) / g["box_printed_m"] > 0.9
+    area = g["sites"] ** 2
+
+    def cover(d_sites):
+        return g["n"] * math.pi * (0.5 * d_sites) ** 2 / area
+
+    d_printed = g["diameter_printed_cm"] * 1e-2 / dx
+    d_read = 0.1 * g["diameter_printed_cm"] * 1e-2 / dx
+    assert abs(d_printed - 160.0) < 0.5 and cover(d_printed) > 30.0
+    assert abs(d_read - 16.0) < 0.05 and 0.35 < cover(d_read) < math.pi / (2.0 * math.sqrt(3.0))
+
+
 def test_golden_table1_gives_one_grid_spacing():
     # Table 1: with the oracle's measured lattice viscosity at each tau, the four
     # (rho_f, mu_f, tau, dt) rows all map to the same grid spacing, 1 mm (D = 15 mm is
