@@ -224,6 +224,17 @@ lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x);
 typedef enum { LBM_STREAM_PULL = 0, LBM_STREAM_INPLACE = 1 } lbm_streaming;
 lbm_status lbm_set_streaming(lbm_ctx* ctx, int mode);
 
+/* Diagnostics of the state at the current step boundary (no counterpart in the paper; for
+ * monitoring long runs). The site moments are those of lbm_get_fields (Eqs. 1-2 with the Guo
+ * half-force, on the populations with the pending IS imposition): out[0] = total mass sum rho
+ * over all sites (fluid and particle sites alike), out[1..3] = total momentum sum rho u,
+ * out[4] = max |u|, out[5] = the lattice Mach number max |u| / c_s (c_s = 1/sqrt(3)), out[6] =
+ * the number of sites whose rho or u is not finite (their moments are left out of out[0..5]).
+ * Sums in a fixed order: the same state gives the same values. Synchronizes.
+ * Returns LBM_E_NAN, with out filled, when out[6] > 0; LBM_E_INVALID if out is NULL; otherwise
+ * the errors of lbm_synchronize. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, double out[7]);
+
 /* ---- Checkpoint and resume ------------------------------------------------------------------
  * No counterpart in the paper. For long runs that must survive the end of a job (the paper's longest sedimentation runs
  * take about 10^5 steps). A checkpoint holds the state at a step boundary: the distributions the

@@ -1,11 +1,12 @@
 """Builds the CUDA library ``liblbmp.so`` in-tree for sm_103a (GB300).
 
-Ten translation units are compiled in parallel with nvcc, one ``-gencode`` each:
+Eleven translation units are compiled in parallel with nvcc, one ``-gencode`` each:
 ``api.cu`` (host C-ABI; host code with -ffp-contract=off), ``sweep_f64.cu`` and
 ``particles.cu`` (-fmad=false: FP64 arithmetic evaluated exactly as written),
 ``sweep_f32.cu``, ``sweep_f16.cu``, ``sweep_bf16.cu`` (FP32 / FP16 / BF16 storage),
 ``noalloc.cu`` (the allocation-free boundary-site exchange), ``batch.cu`` (batched
-ensembles), ``mlp.cu`` (the closure network), ``checkpoint.cu`` (checkpoint and resume).
+ensembles), ``mlp.cu`` (the closure network), ``checkpoint.cu`` (checkpoint and resume),
+``diag.cu`` (state diagnostics, -fmad=false).
 Output: ``paper_1105_2904_gb300/_lib/``.
 """
 from __future__ import annotations
@@ -37,6 +38,7 @@ UNITS = {
     "batch.cu": [],
     "mlp.cu": [],
     "checkpoint.cu": [],
+    "diag.cu": ["-fmad=false"],
 }
 
 

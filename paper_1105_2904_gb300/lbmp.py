@@ -27,7 +27,7 @@ STREAMING = {"pull": LBM_STREAM_PULL, "inplace": LBM_STREAM_INPLACE}
 
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
             "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
-            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_set_sweep_shape", "lbm_set_streaming",
+            "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_set_sweep_shape", "lbm_set_streaming", "lbm_diagnostics",
             "lbm_bs_exchange_noalloc",
             "lbm_checkpoint_size", "lbm_checkpoint_save", "lbm_checkpoint_load", "lbm_get_particles_async",
             "lbm_wait_particles",
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_profile_steps.argtypes = [P, i32, D]
     lib.lbm_set_sweep_shape.argtypes = [P, i32]
     lib.lbm_set_streaming.argtypes = [P, i32]
+    lib.lbm_diagnostics.argtypes = [P, D]
     lib.lbm_get_particles_async.argtypes = [P, P, ctypes.POINTER(ctypes.c_longlong)]
     lib.lbm_wait_particles.argtypes = [P, ctypes.c_longlong]
     lib.lbm_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
@@ -278,6 +279,21 @@ def lbm_set_sweep_shape(h, threads_x):
 
 def lbm_set_streaming(h, mode):
     _check(h, load().lbm_set_streaming(h, int(mode)))
+
+
+def lbm_diagnostics(h):
+    """Totals and extremes of the state (lbm_diagnostics); raises LbmError(LBM_E_NAN) when some
+    site's moments are not finite, with the values in the exception's ``diagnostics``."""
+    out = np.zeros(7)
+    st = load().lbm_diagnostics(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    d = {"mass": out[0], "momentum": out[1:4].copy(), "max_speed": out[4], "mach": out[5],
+         "nonfinite_sites": int(out[6])}
+    try:
+        _check(h, st)
+    except LbmError as e:
+        e.diagnostics = d
+        raise
+    return d
 
 
 def lbm_bs_exchange_noalloc(lattice, nx, ny, nz, walls, body_force, g_ptr, tags_ptr, n, centers_ptr,
@@ -506,6 +522,10 @@ class Simulation:
 
     def profile(self, n):
         return lbm_profile_steps(self.h, n)
+
+    def diagnostics(self):
+        """Total mass and momentum, max |u|, Mach number, non-finite sites (lbm_diagnostics)."""
+        return lbm_diagnostics(self.h)
 
     def checkpoint(self):
         """State at the current step boundary (lbm_checkpoint_save) as a numpy uint8 array."""
