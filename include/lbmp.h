@@ -48,7 +48,9 @@ typedef enum {
     LBM_E_OOM = 2,      /* device allocation failed */
     LBM_E_CUDA = 3,     /* a CUDA call failed (no device, launch error, ...) */
     LBM_E_OVERLAP = 4,  /* particles overlap when added */
-    LBM_E_TIMEOUT = 5,  /* a bounded device wait expired */
+    LBM_E_TIMEOUT = 5,  /* reserved for a bounded device wait that expired; no kernel of this
+                           version waits on another (a step's phases are separate launches in
+                           stream order), so none returns it */
     LBM_E_STATE = 6,    /* call not allowed in the current state (e.g. configure after step) */
     LBM_E_NAN = 7,      /* non-finite value detected in the state */
     LBM_E_CAPACITY = 8, /* a device work list overflowed (e.g. contact pairs) */
