@@ -443,6 +443,10 @@ class Simulation:
         (LBM_EQUILIBRIUM; their axis is walled); wall_velocity: {face: velocity} of no-slip
         faces moving in their plane; streaming: "pull" (two buffers) or "inplace" (one
         buffer, lbm_set_streaming)."""
+        if isinstance(precision, str) and precision not in PRECISIONS:
+            raise ValueError("precision must be one of %s, not %r" % (sorted(PRECISIONS), precision))
+        if isinstance(streaming, str) and streaming not in STREAMING:
+            raise ValueError("streaming must be one of %s, not %r" % (sorted(STREAMING), streaming))
         self.lattice = lattice
         self.Q = 9 if lattice == LBM_D2Q9 else 19
         self.shape = (nz, ny, nx)

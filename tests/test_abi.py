@@ -55,3 +55,14 @@ def test_invalid_arguments_are_rejected_before_device_use(lib):
     assert lib.lbm_create(ctypes.byref(h), 7, 8, 8, 8, 0.7, None) == 1    # unknown lattice
     assert lib.lbm_create(ctypes.byref(h), 1, 0, 8, 8, 0.7, None) == 1    # empty axis
     assert lib.lbm_create(ctypes.byref(h), 1, 2048, 2048, 1024, 0.7, None) == 1  # > 2^31 sites
+
+
+def test_binding_rejects_unknown_names_before_device_use():
+    with pytest.raises(ValueError):
+        lbmp.Simulation(1, 8, 8, 8, 0.7, streaming="aa")
+    with pytest.raises(ValueError):
+        lbmp.Simulation(1, 8, 8, 8, 0.7, precision="fp8")
+    # null context pointers are refused by every entry point that takes one
+    lib = lbmp.load()
+    assert lib.lbm_set_streaming(None, 1) == 1
+    assert lib.lbm_diagnostics(None, None) == 1
