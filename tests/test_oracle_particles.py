@@ -1,8 +1,8 @@
 """Pins of the oracle's particle coupling (Sec. 2.2-2.3, Eqs. 5-19).
 
 Classification is checked against a brute-force classifier written here from the
-definitions (every grid site tested directly, no template); the momentum transfer against
-first-step closed forms; the coupling against exact momentum and mass budgets; the
+definitions (every grid site tested directly, no template); the momentum transfer and the
+internal-site imposition against first-step closed forms; the coupling against exact momentum and mass budgets; the
 rotation sign against spin-down; the hard-core collisions against the conservation laws.
 """
 import math
@@ -410,3 +410,91 @@ def test_rejects_invalid_particles():
         _contact_sim([[15, 15, 20]], [1.2], [1.0])
     with pytest.raises(ValueError):   # too large for the periodic box
         _contact_sim([[15, 15, 20]], [13.5], [1.0])
+
+
+def _feq_np(w, c, rho, u):
+    """Second-order equilibrium of every direction for velocities u[..., 3] (R1)."""
+    cu = np.tensordot(u, c.T.astype(np.float64), axes=([-1], [0]))      # [..., Q]
+    usq = (u * u).sum(-1)[..., None]
+    return w * rho[..., None] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq)
+
+
+@pytest.mark.parametrize("lattice", [O.D2Q9, O.D3Q19])
+def test_first_step_internal_site_imposition_closed_form(lattice):
+    # Fluid at rest (f = w_i), one particle translating fast enough that its first move
+    # crosses a shift boundary on two axes (s' = (+1, -1, 0)) and spinning. Everything the
+    # step does is then fixed by closed forms, and the whole state after one step is
+    # predicted site by site:
+    #   - collision leaves f* = w_i everywhere (rest state, no force);
+    #   - old BS sites y (shift 0) take f^eq(rho_B, U + omega x (y - x0)) (Eqs. 5-7);
+    #   - u' = U - dP/m, omega' = omega - dL/I (Eqs. 8-11), x' = x0 + u' (Eq. 13);
+    #   - IS sites of the *shifted* set take f^eq(rho_I, u' + omega' x (y - c')) with
+    #     c' = x0 + s' and rho_I the site's own post-collision density (Eq. 12, R3-R5);
+    #     every other site keeps its post-collision value;
+    #   - propagation moves f*_i(y) to y + c_i.
+    # A mistake in the imposition (the velocities before the acceleration, the site set
+    # before the move, the lever arm on the wrong side of the cross product) changes the
+    # predicted populations by O(1e-2) at hundreds of sites.
+    c, w = O.lattice_tables(lattice)
+    D = 2 if lattice == O.D2Q9 else 3
+    shape = (1, 36, 40) if D == 2 else (22, 24, 26)
+    nz, ny, nx = shape
+    x0 = np.array([19.37, 17.71, 10.58 if D == 3 else 0.0])
+    r, rho_p = 4.6, 3.0
+    U = np.array([0.78, -0.8, 0.05 if D == 3 else 0.0])
+    om = np.array([0.0, 0.0, 0.03]) if D == 2 else np.array([0.012, -0.02, 0.017])
+    s = _sim(lattice, shape, tau=0.8)
+    s.add_particles(x0[None], [r], [rho_p], velocities=U[None], omegas=om[None])
+    s.step(1)
+
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    Y = np.stack([xx, yy, zz], axis=-1).astype(np.float64)      # site coordinates [z,y,x,3]
+    # post-collision state: the rest weights (summed in the oracle's order for rho)
+    fstar = np.broadcast_to(w, shape + (len(w),)).copy()
+    old = brute_force_tags(lattice, shape, (0, 0, 0), [(x0, r, np.zeros(3))])
+    bs_old = (old >> 30) == 1
+    rho_rest = 0.0
+    for wi in w:
+        rho_rest += wi
+    arms = Y[bs_old] - x0
+    arms[:, D:] = 0.0
+    uB = U + np.cross(om, arms)
+    fstar[bs_old] = _feq_np(w, c, np.full(len(arms), rho_rest), uB)
+    dP = (rho_rest * uB).sum(0)
+    dL = np.cross(arms, rho_rest * uB).sum(0)
+    m = rho_p * ((4.0 / 3.0) * math.pi * r ** 3 if D == 3 else math.pi * r ** 2)
+    I = (0.4 if D == 3 else 0.5) * m * r * r
+    u1 = U - dP / m
+    om1 = om - dL / I
+    if D == 2:
+        om1[:2] = 0.0
+        u1[2] = 0.0
+    x1 = x0 + u1
+    shift = np.floor(x1 - x0 + 0.5)
+    shift[D:] = 0
+    assert shift.tolist()[:2] == [1.0, -1.0]                    # the move crosses two boundaries
+
+    p = s.get_particles()
+    np.testing.assert_allclose(p["u"][0], u1, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(p["omega"][0], om1, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(p["x"][0], x1, rtol=0, atol=1e-13)
+    new = brute_force_tags(lattice, shape, (0, 0, 0), [(x0, r, shift)])
+    np.testing.assert_array_equal(s.get_tags(), new)
+    is_new = (new >> 30) == 0
+    left = ((old >> 30) == 0) & ~is_new
+    assert is_new.sum() > 20 and left.sum() > 5 and (bs_old & is_new).sum() > 5
+
+    rho_I = fstar[is_new].sum(-1)
+    arms1 = Y[is_new] - (x0 + shift)
+    arms1[:, D:] = 0.0
+    fstar[is_new] = _feq_np(w, c, rho_I, u1 + np.cross(om1, arms1))
+    expect = np.empty((len(w),) + shape)
+    for i, ci in enumerate(c):
+        expect[i] = np.roll(fstar[..., i], shift=(ci[2], ci[1], ci[0]), axis=(0, 1, 2))
+    got = s.get_f()
+    np.testing.assert_allclose(got, expect, rtol=0, atol=2e-15)
+    # the IS sites the particle left keep their collided (rest) populations, w_i up to the
+    # collision's round-off
+    for i, ci in enumerate(c):
+        moved = np.roll(left, shift=(ci[2], ci[1], ci[0]), axis=(0, 1, 2))
+        np.testing.assert_allclose(got[i][moved], w[i], rtol=0, atol=2e-16)
