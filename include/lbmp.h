@@ -167,16 +167,20 @@ lbm_status lbm_get_particles_async(lbm_ctx* ctx, double* dst, long long* ticket)
  * before it). LBM_E_INVALID for an unknown or already waited ticket. */
 lbm_status lbm_wait_particles(lbm_ctx* ctx, long long ticket);
 
-/* Full distribution state f[Q][N] at the current step boundary (post-propagation, with
- * the IS imposition applied), converted to double. Synchronizes. */
+/* Full distribution state f[Q][N] at the current step boundary: the populations f_i(x, t)
+ * of Sec. 2.1 (Eq. 3) after propagation, with the IS imposition of Eq. 12 applied, converted
+ * to double. Synchronizes. */
 lbm_status lbm_get_distributions(lbm_ctx* ctx, double* f);
 
-/* Replaces the distribution state by f[Q][N] (same layout as lbm_get_distributions).
- * Values are rounded to the storage precision. Synchronizes. */
+/* Replaces the distribution state, the populations f_i(x, t) of Sec. 2.1 (Eq. 3) at a step
+ * boundary, by f[Q][N] (same layout as lbm_get_distributions). Values are rounded to the
+ * storage precision. Synchronizes. */
 lbm_status lbm_set_distributions(lbm_ctx* ctx, const double* f);
 
-/* Owner map of the lattice sites, tags[N] (unsigned 32-bit): (class << 30) | particle id
- * with class 0 = IS, 1 = BS, 2 = other solid site; 0xFFFFFFFF = fluid. Where the site
+/* Owner map of the lattice sites, tags[N] (unsigned 32-bit): the boundary sites (BS) and
+ * internal sites (IS) of each particle (Sec. 2.2, Fig. 2) at its current whole-site shift
+ * (Eqs. 14-15): (class << 30) | particle id with class 0 = IS, 1 = BS, 2 = other solid
+ * site; 0xFFFFFFFF = fluid. Where the site
  * sets of close particles meet, IS wins over BS over the rest, then the lower id.
  * Synchronizes. */
 lbm_status lbm_get_masks(lbm_ctx* ctx, unsigned* tags);
@@ -283,6 +287,13 @@ lbm_status lbm_checkpoint_load(lbm_ctx* ctx, const void* buf, unsigned long long
  * torque = -sum r x dp (the force and torque lbm_get_particles reports for a step taken
  * from that state).
  *
+ * centers[p] is the centre of particle p's site set, not its position x_p: the sites are
+ * the set classified around the centre x_p0 at which the particle was added, translated by
+ * the whole-site shift s_p = floor(x_p - x_p0 + 1/2) per axis (Eqs. 14-15), and the lever
+ * arms of a step are taken from x_p0 + s_p. Before a particle first moves that is x_p0;
+ * a caller who passes the x_p that lbm_get_particles reports after the particle has moved
+ * by a fraction of a site gets other rigid-body velocities and torques.
+ *
  * Arguments: lattice and sizes as lbm_create; walls[3] (may be NULL: all periodic) flags the
  * axes with solid walls (no minimum image there); body_force[3] the fluid force density F
  * (may be NULL). Device pointers, caller-owned: g[Q][N] FP32 deviations f_i - w_i of the
@@ -298,8 +309,13 @@ lbm_status lbm_checkpoint_load(lbm_ctx* ctx, const void* buf, unsigned long long
  * call's sums afterwards. Calls that overlap on the GPU (different streams, or devices
  * sharing nothing else) race on that array and must be serialised by the caller. The first
  * call on each device looks up the array's device address (a CUDA runtime query, no
- * allocation); make that first call before any stream capture. No cudaMalloc, cudaFree or
- * allocating library routine is called. LBM_E_CUDA if the device query or a launch fails. */
+ * allocation) and keeps it for the life of the process; make that first call before any
+ * stream capture. A device reset (cudaDeviceReset) reloads the library's device image at
+ * another address, so the call is not supported on a device that was reset after its first
+ * call there. No cudaMalloc, cudaFree or allocating library routine is called.
+ * LBM_E_CUDA, with nothing enqueued, if a CUDA error from earlier work is still pending on
+ * the calling thread (it is left for its owner to read) or the device query fails; LBM_E_CUDA
+ * if one of the call's own launches fails. */
 lbm_status lbm_bs_exchange_noalloc(int lattice, int nx, int ny, int nz, const int walls[3],
                                    const double body_force[3], const float* g,
                                    const unsigned* tags, int n, const double* centers,

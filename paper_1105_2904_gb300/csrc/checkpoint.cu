@@ -19,7 +19,7 @@ using namespace lbmp::host;
 namespace {
 
 constexpr char kMagic[8] = {'L', 'B', 'M', 'P', 'C', 'K', 'P', '1'};
-constexpr int kVersion = 2;
+constexpr int kVersion = 3;
 
 struct CkptHeader {
     char magic[8];
@@ -55,6 +55,7 @@ unsigned long long fingerprint(const lbm_ctx* ctx)
     f.val(ctx->g.ny);
     f.val(ctx->g.nz);
     for (int k = 0; k < 3; ++k) f.val(ctx->g.wall[k]);
+    f.val(ctx->g.eqface);  // no-slip and equilibrium faces both set wall[k]
     f.val(ctx->precision);
     f.val(ctx->inplace);
     f.val(ctx->tau);

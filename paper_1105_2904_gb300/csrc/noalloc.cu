@@ -115,7 +115,9 @@ __global__ void k_noalloc_finish(const double* acc, int n, double* force, double
         }
 }
 
-// Address of the static accumulator array on the current device (looked up once per device).
+// Address of the static accumulator array on the current device, looked up once per device
+// ordinal and kept for the life of the process (a device reset, which would move the array,
+// is not supported after the first call on that device).
 lbm_status accumulator_address(double** out)
 {
     int dev = -1;
@@ -151,6 +153,9 @@ extern "C" lbm_status lbm_bs_exchange_noalloc(int lattice, int nx, int ny, int n
     if (n < 0 || n > LBM_NOALLOC_MAX_PARTICLES) return LBM_E_INVALID;
     if (!g || !tags || (n > 0 && (!centers || !velocities || !omegas || !force || !torque))) return LBM_E_INVALID;
     if (n == 0) return LBM_OK;
+    // An error left by earlier work is not this call's: report it without clearing it, and
+    // launch nothing, so that every error read after a launch below belongs to that launch.
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_E_CUDA;
     double* acc = nullptr;
     const lbm_status st = accumulator_address(&acc);
     if (st != LBM_OK) return st;
@@ -176,11 +181,13 @@ extern "C" lbm_status lbm_bs_exchange_noalloc(int lattice, int nx, int ny, int n
     a.omega = omegas;
     a.acc = acc;
     k_noalloc_clear<<<(6 * n + 255) / 256, 256, 0, s>>>(acc, 6 * n);
+    if (cudaGetLastError() != cudaSuccess) return LBM_E_CUDA;
     const dim3 grid((nx + 127) / 128, ny, nz);
     if (lattice == LBM_D2Q9)
         k_noalloc_exchange<D2Q9><<<grid, 128, 0, s>>>(a);
     else
         k_noalloc_exchange<D3Q19><<<grid, 128, 0, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return LBM_E_CUDA;
     k_noalloc_finish<<<(n + 127) / 128, 128, 0, s>>>(acc, n, force, torque);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }

@@ -91,3 +91,26 @@ def test_checkpoint_of_a_different_setup_is_refused():
         g.restore(ck[:100])                # truncated
     other.close()
     g.close()
+
+
+def test_checkpoint_with_other_face_kinds_is_refused():
+    # Equilibrium faces and no-slip faces on the same axis are both walls; a checkpoint of one
+    # must not load into the other (the saved face velocities drive different rules).
+    def make(eq):
+        faces = {4: (0.0, 0.0, 0.0), 5: (0.01, 0.0, 0.0)} if eq else None
+        g = lbmp.Simulation(1, *DIMS, 0.7, precision="fp32", walls=(0, 0, 1), equilibrium_faces=faces)
+        if not eq:
+            g.set_wall_velocity(5, (0.01, 0.0, 0.0))
+        return g
+    a, b = make(True), make(False)
+    a.step(3)
+    b.step(3)
+    ca, cb = a.checkpoint(), b.checkpoint()
+    with pytest.raises(lbmp.LbmError):
+        b.restore(ca)
+    with pytest.raises(lbmp.LbmError):
+        a.restore(cb)
+    a.restore(ca)
+    b.restore(cb)
+    a.close()
+    b.close()

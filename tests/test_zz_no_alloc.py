@@ -5,7 +5,10 @@ their own pool, allocation forbidden while recording work or inside a real-time 
 pass all buffers and the library only uses a fixed device array of its own. Here the force
 and torque it returns for a state are checked against what lbm_step + lbm_get_particles
 report for one step from the same state, with the FP32 tolerances of the parity tests, on
-two calls in a row (the second call must not see the first call's sums)."""
+two calls in a row (the second call must not see the first call's sums): for the state the
+particles were added in, and for a state reached after the particles have moved by
+fractions of a site and some have changed their whole-site shift, where the centres passed
+are those of the site sets, x_p0 + floor(x_p - x_p0 + 1/2), not the positions x_p."""
 import math
 
 import numpy as np
@@ -41,12 +44,14 @@ def _case(lattice):
     return dims, walls, F, c, r, v, om, dens
 
 
+@pytest.mark.parametrize("steps_before", [0, 90], ids=["at_start", "moved"])
 @pytest.mark.parametrize("lattice", [lbmp.LBM_D3Q19, lbmp.LBM_D2Q9], ids=["d3q19", "d2q9"])
-def test_noalloc_exchange_matches_the_context_step(lattice):
+def test_noalloc_exchange_matches_the_context_step(lattice, steps_before):
     import torch
 
     dims, walls, F, c, r, v, om, dens = _case(lattice)
     nx, ny, nz = dims
+    D = 3 if lattice == lbmp.LBM_D3Q19 else 2
     _, w = O.lattice_tables(lattice)
     Q, N = len(w), nx * ny * nz
     xi = W.perturbation(Q, (nz, ny, nx), seed=77)
@@ -55,17 +60,27 @@ def test_noalloc_exchange_matches_the_context_step(lattice):
     sim = lbmp.Simulation(lattice, nx, ny, nz, 0.7, body_force=F, precision="fp32", walls=walls)
     sim.set_f(f0)
     sim.add_particles(c, r, dens, v, om)
+    sim.step(steps_before)
+    f_start = sim.get_f()
     tags = sim.get_tags()
+    p = sim.get_particles()
+    # centre of each particle's site set: the initial centre moved by whole sites (Eqs. 14-15)
+    centre = np.array(c, dtype=np.float64).copy()
+    centre[:, :D] += np.floor((p["x"][:, :D] - centre[:, :D]) + 0.5)
+    if steps_before:
+        frac = np.abs(p["x"][:, :D] - centre[:, :D])
+        assert np.any(centre[:, :D] != np.asarray(c)[:, :D])      # some shift changed
+        assert np.any((frac > 0.05) & (frac < 0.45))             # away from the site-set centre
     sim.step(1)
     ref = sim.get_particles()
     sim.close()
 
     dev = "cuda"
-    g = torch.tensor((f0 - w[:, None, None, None]).reshape(Q, N), dtype=torch.float32, device=dev)
+    g = torch.tensor((f_start - w[:, None, None, None]).reshape(Q, N), dtype=torch.float32, device=dev)
     t = torch.from_numpy(np.ascontiguousarray(tags.reshape(-1)).view(np.int32)).to(dev)
-    cen = torch.tensor(c, dtype=torch.float64, device=dev)
-    vel = torch.tensor(v, dtype=torch.float64, device=dev)
-    omg = torch.tensor(om, dtype=torch.float64, device=dev)
+    cen = torch.tensor(centre, dtype=torch.float64, device=dev)
+    vel = torch.tensor(p["u"], dtype=torch.float64, device=dev)
+    omg = torch.tensor(p["omega"], dtype=torch.float64, device=dev)
     n = len(r)
     force = torch.empty((n, 3), dtype=torch.float64, device=dev)
     torque = torch.empty((n, 3), dtype=torch.float64, device=dev)
