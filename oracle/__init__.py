@@ -22,8 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liblbm_oracle.so")
+_SO_OMP = os.path.join(_BUILD, "liblbm_oracle_omp.so")
 _LOCK = threading.Lock()
 _LIB = None
+_LIB_OMP = None
 
 D2Q9 = 0
 D3Q19 = 1
@@ -32,26 +34,33 @@ CLS_IS, CLS_BS, CLS_IN = 0, 1, 2
 TAG_FLUID = 0xFFFFFFFF
 
 
-def build(force: bool = False) -> str:
-    """Compiles the oracle into ``oracle/_build/liblbm_oracle.so`` (gcc, FP64)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compiles the oracle into ``oracle/_build/liblbm_oracle.so`` (gcc, FP64, one thread).
+
+    openmp=True builds ``liblbm_oracle_omp.so`` from the same source with ``-fopenmp``: the
+    collision and propagation loops are split between threads, each site's arithmetic is
+    unchanged, so the results are identical to the single-threaded build (a CPU test checks
+    that). It serves the timed all-core CPU baseline and long parity runs on large boxes.
+    """
     os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+    so = _SO_OMP if openmp else _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "lbm_oracle.h"))
     ):
-        return _SO
-    tmp = _SO + ".%d.tmp" % os.getpid()
+        return so
+    tmp = so + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-Wall",
-           "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+           "-shared", "-fPIC"] + (["-fopenmp"] if openmp else ["-Wno-unknown-pragmas"]) + [_SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
 
 
-def _lib():
-    global _LIB
+def _lib(openmp: bool = False):
+    global _LIB, _LIB_OMP
     with _LOCK:
-        if _LIB is None:
-            lib = ctypes.CDLL(build())
+        if (_LIB_OMP if openmp else _LIB) is None:
+            lib = ctypes.CDLL(build(openmp=openmp))
             P = ctypes.c_void_p
             D = ctypes.POINTER(ctypes.c_double)
             I = ctypes.POINTER(ctypes.c_int)
@@ -71,13 +80,17 @@ def _lib():
             lib.osim_get_fields.argtypes = [P, D, D]
             lib.osim_get_particles.argtypes = [P, D, D, D, D, D]
             lib.osim_get_tags.argtypes = [P, U]
+            lib.osim_get_orientations.argtypes = [P, D]
             lib.osim_get_diagnostics.argtypes = [P, D]
             lib.osim_num_particles.argtypes = [P]
             lib.osim_get_template.argtypes = [P, ctypes.c_int, I]
             lib.osim_resolve_contacts.argtypes = [P, D]
             lib.osim_collide_site.argtypes = [P, D, D]
-            _LIB = lib
-    return _LIB
+            if openmp:
+                _LIB_OMP = lib
+            else:
+                _LIB = lib
+    return _LIB_OMP if openmp else _LIB
 
 
 def _dp(a):
@@ -96,8 +109,10 @@ class OracleSim:
 
     def __init__(self, lattice, nx, ny, nz, tau, body_force=(0.0, 0.0, 0.0),
                  walls=(0, 0, 0), gravity=(0.0, 0.0, 0.0), gap=0.0, body_force_on_particles=False,
-                 wall_velocity=None, equilibrium_faces=None):
-        self.lib = _lib()
+                 wall_velocity=None, equilibrium_faces=None, openmp=False):
+        """openmp: use the OpenMP build (same arithmetic, identical results, all cores;
+        thread count from OMP_NUM_THREADS)."""
+        self.lib = _lib(openmp)
         self.lattice = lattice
         self.Q = 9 if lattice == D2Q9 else 19
         self.shape = (nz, ny, nx)
@@ -169,6 +184,12 @@ class OracleSim:
         out = [np.zeros((n, 3), dtype=np.float64) for _ in range(5)]
         self.lib.osim_get_particles(self.h, *[_dp(a) for a in out])
         return dict(zip(("x", "u", "omega", "force", "torque"), out))
+
+    def get_orientations(self):
+        q = np.zeros((self.num_particles, 4), dtype=np.float64)
+        if len(q):
+            self.lib.osim_get_orientations(self.h, _dp(q))
+        return q
 
     def get_tags(self):
         t = np.empty(self.shape, dtype=np.uint32)

@@ -10,7 +10,8 @@
  *   3. particle acceleration (Eqs. 10-11),
  *   4. hard-core particle-particle and particle-wall collisions (Sec. 2.3, Eqs. 16-19),
  *      "part of the particle's acceleration substep",
- *   5. position update (Eqs. 13-15),
+ *   5. position update (Eqs. 13-15) and orientation (a unit quaternion turned by the angular
+ *      velocity over the step),
  *   6. velocity of the internal sites at the new position (Eq. 12),
  *   7. propagation (Eq. 3, left-hand side), with halfway bounce-back at solid walls.
  *
@@ -73,6 +74,7 @@ typedef struct {
     double phi[3];   /* x0 - A, fractional part */
     double x[3], u[3], om[3];
     double r, inv_m, inv_I, inv_rho, ext[3];
+    double q[4];     /* orientation, unit quaternion (w, x, y, z); identity when added */
     int s[3];        /* integer shift of the site set (R3) */
     int nt;          /* number of solid sites in the template */
     int* tmpl;       /* nt entries of (ox, oy, oz, class) relative to A */
@@ -281,6 +283,28 @@ static void lever_arm(const opart* P, const int* o, double r[3])
     for (int k = 0; k < 3; k++) r[k] = (double)o[k] - P->phi[k];
 }
 
+/* Orientation update of the rigid-body integration (Sec. 2.2: the particle moves with the
+ * velocities of Eqs. 10-11 over the step, Eq. 13 for the position). The orientation is the
+ * unit quaternion q = (w, x, y, z); turning at the angular velocity omega (space frame),
+ * held over the step dt = 1, rotates the body by theta = |omega| about omega/|omega|:
+ * q' = dq q with dq = (cos(theta/2), sin(theta/2) omega/|omega|) (Hamilton product,
+ * dq applied in the space frame), then q' is divided by its norm. The spheres' dynamics
+ * do not depend on it; it is bookkeeping of the body's attitude. */
+static void rotate_orientation(double q[4], const double om[3])
+{
+    double th = sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
+    if (th == 0.0) return;
+    double c = cos(0.5 * th), sn = sin(0.5 * th) / th;
+    double d[4] = {c, sn * om[0], sn * om[1], sn * om[2]};
+    double r[4];
+    r[0] = d[0] * q[0] - (d[1] * q[1] + d[2] * q[2] + d[3] * q[3]);
+    r[1] = d[0] * q[1] + q[0] * d[1] + (d[2] * q[3] - d[3] * q[2]);
+    r[2] = d[0] * q[2] + q[0] * d[2] + (d[3] * q[1] - d[1] * q[3]);
+    r[3] = d[0] * q[3] + q[0] * d[3] + (d[1] * q[2] - d[2] * q[1]);
+    double nrm = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    for (int k = 0; k < 4; k++) q[k] = r[k] / nrm;
+}
+
 static double min_image(double d, int n, int periodic)
 {
     if (!periodic) return d;
@@ -389,6 +413,8 @@ int osim_add_particles(osim* s, int n, const double* centers, const double* radi
             p->phi[k] = p->x0[k] - (double)p->A[k];
             p->s[k] = 0;
         }
+        p->q[0] = 1.0;
+        p->q[1] = p->q[2] = p->q[3] = 0.0;
         for (int k = 0; k < D; k++) {
             int nk = axis_len(s, k);
             if (s->walls[k]) {
@@ -514,12 +540,14 @@ static void step_once(osim* s)
     const olat* L = &s->L;
     const int Q = L->Q, D = L->D;
     const long N = s->N;
-    double fin[MAXQ] = {0}, fout[MAXQ] = {0};
     s->started = 1;
     for (int k = 0; k < 6; k++) s->diag[k] = 0.0;
 
-    /* 1. Collision at every site. */
+    /* 1. Collision at every site. (The sites are independent; an OpenMP build splits this
+     * loop and the propagation loop between threads without changing any site's arithmetic.) */
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < N; x++) {
+        double fin[MAXQ] = {0}, fout[MAXQ] = {0};
         for (int i = 0; i < Q; i++) fin[i] = s->f[(long)i * N + x];
         collide(s, fin, fout);
         for (int i = 0; i < Q; i++) s->fp[(long)i * N + x] = fout[i];
@@ -590,6 +618,7 @@ static void step_once(osim* s)
             P->x[k] = P->x[k] + P->u[k];
             P->s[k] = (int)floor((P->x[k] - P->x0[k]) + 0.5);
         }
+        rotate_orientation(P->q, P->om);
     }
     free(un);
     if (s->np > 0) rebuild_tags(s);
@@ -615,7 +644,9 @@ static void step_once(osim* s)
         }
     }
 
-    /* 7. Propagation; halfway bounce-back where a move would cross a solid wall. */
+    /* 7. Propagation; halfway bounce-back where a move would cross a solid wall. Every
+     * (site, direction) has its own target, so z-planes are independent. */
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < s->nz; z++)
         for (int y = 0; y < s->ny; y++)
             for (int x = 0; x < s->nx; x++) {
@@ -689,6 +720,12 @@ void osim_get_particles(const osim* s, double* x, double* u, double* omega, doub
             if (torque) torque[3 * p + k] = -P->dL[k];
         }
     }
+}
+
+void osim_get_orientations(const osim* s, double* q)
+{
+    for (int p = 0; p < s->np; p++)
+        for (int k = 0; k < 4; k++) q[4 * p + k] = s->P[p].q[k];
 }
 
 void osim_get_tags(const osim* s, unsigned* tags) { memcpy(tags, s->tag, sizeof(unsigned) * (size_t)s->N); }

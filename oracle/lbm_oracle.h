@@ -55,6 +55,9 @@ void osim_get_fields(const osim* s, double* rho, double* u);
 void osim_get_particles(const osim* s, double* x, double* u, double* omega,
                         double* force, double* torque);
 void osim_get_tags(const osim* s, unsigned* tags);
+/* Orientation of each particle, n*4: unit quaternion (w, x, y, z), identity when added,
+ * turned every step by |omega| about omega (space frame) after the acceleration. */
+void osim_get_orientations(const osim* s, double* q);
 /* Momentum handed to the fluid in the last step: diag[0..2] = sum of dP_B over all
  * particles, diag[3..5] = momentum change caused by the IS imposition. */
 void osim_get_diagnostics(const osim* s, double* diag);

@@ -498,3 +498,68 @@ def test_first_step_internal_site_imposition_closed_form(lattice):
     for i, ci in enumerate(c):
         moved = np.roll(left, shift=(ci[2], ci[1], ci[0]), axis=(0, 1, 2))
         np.testing.assert_allclose(got[i][moved], w[i], rtol=0, atol=2e-16)
+
+
+# ---- orientation (rigid-body rotation integrated with the position) -------------------
+
+def _quat_matrix(q):
+    """Rotation matrix of a unit quaternion (w, x, y, z)."""
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _rodrigues(om):
+    """Rotation by |om| about om / |om| (Rodrigues' formula)."""
+    th = np.linalg.norm(om)
+    if th == 0.0:
+        return np.eye(3)
+    k = om / th
+    K = np.array([[0.0, -k[2], k[1]], [k[2], 0.0, -k[0]], [-k[1], k[0], 0.0]])
+    return np.eye(3) + math.sin(th) * K + (1.0 - math.cos(th)) * (K @ K)
+
+
+@pytest.mark.parametrize("lattice", [O.D2Q9, O.D3Q19])
+def test_orientation_of_a_steadily_turning_particle(lattice):
+    # A fixed particle (infinite density: its velocities never change) turning at omega:
+    # after n steps its orientation is the rotation by n |omega| about omega, i.e. the
+    # quaternion (cos(n th / 2), sin(n th / 2) omega / th), and stays of unit norm.
+    D = 2 if lattice == O.D2Q9 else 3
+    shape = (1, 32, 32) if D == 2 else (20, 20, 20)
+    om = np.array([0.0, 0.0, 0.0371]) if D == 2 else np.array([0.021, -0.013, 0.0298])
+    s = _sim(lattice, shape)
+    s.add_particles([[10.3, 11.6, 9.2 if D == 3 else 0.0]], [4.2], [math.inf], omegas=om[None])
+    np.testing.assert_array_equal(s.get_orientations(), [[1.0, 0.0, 0.0, 0.0]])
+    th = np.linalg.norm(om)
+    done = 0
+    for n in (1, 7, 60):
+        s.step(n - done)
+        done = n
+        q = s.get_orientations()[0]
+        expect = np.concatenate([[math.cos(0.5 * n * th)], math.sin(0.5 * n * th) * om / th])
+        np.testing.assert_allclose(q, expect, rtol=0, atol=2e-15 * n)
+        assert abs(np.dot(q, q) - 1.0) < 1e-15
+
+
+def test_orientation_turns_in_the_space_frame_each_step():
+    # A light particle that moves and spins in still fluid: the fluid torque turns its
+    # angular velocity away from its initial axis. Each step the orientation must advance by
+    # the rotation through |omega'| about omega', the angular velocity after that step's
+    # acceleration (Eq. 11), applied in the space frame: R(q_n+1) = Rot(omega') R(q_n).
+    shape = (24, 24, 24)
+    s = _sim(O.D3Q19, shape, tau=0.7)
+    s.add_particles([[11.3, 12.6, 11.8]], [5.2], [0.6], velocities=[[0.02, -0.01, 0.015]],
+                    omegas=[[0.01, 0.04, -0.02]])
+    R = _quat_matrix(s.get_orientations()[0])
+    om_first = None
+    for n in range(40):
+        s.step(1)
+        om = s.get_particles()["omega"][0]
+        om_first = om if om_first is None else om_first
+        Rn = _quat_matrix(s.get_orientations()[0])
+        np.testing.assert_allclose(Rn @ R.T, _rodrigues(om), rtol=0, atol=1e-14)
+        R = Rn
+    # the axis did turn, so the order of the rotations matters in this test
+    cosang = np.dot(om, om_first) / (np.linalg.norm(om) * np.linalg.norm(om_first))
+    assert cosang < 0.99
