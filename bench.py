@@ -45,6 +45,9 @@ def parse():
                    choices=["d3q19_512", "d2q9_sedimentation", "ensemble_64", "closure"])
     p.add_argument("--closure-cells", type=int, nargs=2, default=[512, 64],
                    help="closure workload: training and held-out cells (8 spheres each)")
+    p.add_argument("--closure-large-cells", type=int, default=0,
+                   help="closure workload: also judge the trained network on this many held-out 128^3 "
+                        "cells with 200 spheres of radius 3 against their 512^3 radius-12 twins")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     p.add_argument("--edge", type=int, default=0, help="override the 3D box edge (same solid fraction)")
     p.add_argument("--sweep-shape", type=int, default=-1,
@@ -53,6 +56,13 @@ def parse():
                    help="streaming scheme (lbm_set_streaming): pull (two buffers) or inplace (one buffer)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-patterns", action="store_true",
+                   help="default workload: leave out the 16-bit storages, the batched ensemble and the "
+                        "learned closure measured beside the headline line")
+    p.add_argument("--pattern-closure-cells", type=int, nargs=2, default=[256, 32],
+                   help="training and held-out cells of the closure measured beside the headline line")
+    p.add_argument("--cpu-full", action="store_true",
+                   help="also time the all-core oracle on the full-size 3D workload for 10 steps")
     return p.parse_args()
 
 
@@ -179,12 +189,12 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(wl, target_s=12.0, precision=None, shape=-1, streaming="pull"):
+def cpu_baseline(wl, target_s=12.0, configs=()):
     """The FP64 oracle, as it stands (one host thread), on a bounded sample of the workload:
-    the same suspension scaled to a smaller periodic box with the same solid fraction. With a
-    precision, the CUDA path then runs the same sample for the same steps in that storage and
-    the error of the bench line's configuration against the oracle is returned beside the
-    baseline: (baseline, error)."""
+    the same suspension scaled to a smaller periodic box with the same solid fraction.
+    configs: (precision, sweep shape, streaming) triples; for each, the CUDA path then runs the
+    same sample for the same steps in that configuration, and its error against the oracle is
+    returned beside the baseline: (baseline, [error per config])."""
     import oracle as O
 
     edge = 64 if wl.lattice == "D3Q19" else 256
@@ -213,30 +223,74 @@ def cpu_baseline(wl, target_s=12.0, precision=None, shape=-1, streaming="pull"):
     sim.step(steps)
     dt = time.perf_counter() - t
     base = {"value": sites * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%s, %d steps, %.1f s, single-threaded FP64 C" % (sample, steps, dt)}
-    if precision is None:
-        return base
-    from paper_1105_2904_gb300 import lbmp
+            "sample": "%s, %d steps, %.1f s, single-threaded FP64 C" % (sample, steps, dt),
+            "host": host_info()}
+    # The same oracle built with OpenMP over its site loops (identical results), all cores.
     if wl.lattice == "D3Q19":
-        g = lbmp.Simulation(1, edge, edge, edge, s.tau, body_force=s.body_force, precision=precision,
-                            body_force_on_particles=s.body_force_on_particles, streaming=streaming)
+        par = O.OracleSim(O.D3Q19, edge, edge, edge, s.tau, body_force=s.body_force,
+                          body_force_on_particles=s.body_force_on_particles, openmp=True)
     else:
-        g = lbmp.Simulation(0, edge, 2 * edge, 1, wl.tau, precision=precision, walls=wl.walls, gravity=wl.gravity,
-                            streaming=streaming)
-    g.set_sweep_shape(shape)
-    g.add_particles(c, r, d, v)
-    g.step(1 + steps)
-    _, ug = g.get_fields()
-    pg = g.get_particles()
-    g.close()
+        par = O.OracleSim(O.D2Q9, edge, 2 * edge, 1, wl.tau, walls=wl.walls, gravity=wl.gravity,
+                          gap=0.0, openmp=True)
+    par.add_particles(c, r, d, v)
+    par.step(1)
+    t = time.perf_counter()
+    par.step(steps)
+    dtp = time.perf_counter() - t
+    del par
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    base["all_cores"] = {"value": sites * steps / dtp / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "the same sample and steps, %.1f s, FP64 C with OpenMP over the site loops "
+                                   "(identical results)" % dtp}
+    if not configs:
+        return base, []
+    from paper_1105_2904_gb300 import lbmp
     _, ur = sim.get_fields()
     pr = sim.get_particles()
-    err = {"velocity": float(np.max(np.abs(ug - ur)) / np.max(np.abs(ur))),
-           "force": float(np.max(np.abs(pg["force"] - pr["force"])) / np.max(np.abs(pr["force"]))),
-           "norm": "max |x - x_oracle| / max |x_oracle| over the field (velocity) or the particles (force)",
-           "sample": "%s, %d steps, same storage, streaming and sweep shape as the timed run"
-                     % (sample, 1 + steps)}
-    return base, err
+    errs = []
+    for precision, shape, streaming in configs:
+        if wl.lattice == "D3Q19":
+            g = lbmp.Simulation(1, edge, edge, edge, s.tau, body_force=s.body_force, precision=precision,
+                                body_force_on_particles=s.body_force_on_particles, streaming=streaming)
+        else:
+            g = lbmp.Simulation(0, edge, 2 * edge, 1, wl.tau, precision=precision, walls=wl.walls,
+                                gravity=wl.gravity, streaming=streaming)
+        g.set_sweep_shape(shape)
+        g.add_particles(c, r, d, v)
+        g.step(1 + steps)
+        _, ug = g.get_fields()
+        pg = g.get_particles()
+        g.close()
+        errs.append({"velocity": float(np.max(np.abs(ug - ur)) / np.max(np.abs(ur))),
+                     "force": float(np.max(np.abs(pg["force"] - pr["force"])) / np.max(np.abs(pr["force"]))),
+                     "norm": "max |x - x_oracle| / max |x_oracle| over the field (velocity) or the particles (force)",
+                     "sample": "%s, %d steps, %s storage, the timed run's streaming and sweep shape"
+                               % (sample, 1 + steps, precision)})
+    return base, errs
+
+
+def host_info():
+    """Host cores and CPU model of the machine the baseline ran on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def run_reference(args):
@@ -400,9 +454,47 @@ def run_ours(args):
                            "followed by a read-back of the particle state to host arrays (asynchronous, "
                            "double-buffered in pinned memory)" % args.steps}
 
-    cpu, err = None, None
+    want_patterns = (rank == 0 and world == 1 and not args.no_patterns and args.workload == "d3q19_512"
+                     and not args.edge and args.precision == "fp32" and args.streaming == "pull")
+    cpu, err, errs = None, None, []
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, err = cpu_baseline(wl, precision=args.precision, shape=args.sweep_shape, streaming=args.streaming)
+        configs = [(args.precision, args.sweep_shape, args.streaming)]
+        if want_patterns:
+            configs += [("fp16", -1, "pull"), ("bf16", -1, "pull")]
+        cpu, errs = cpu_baseline(wl, configs=configs)
+        err = errs[0]
+        if args.cpu_full and lattice == 1:
+            cpu["full_size"] = cpu_full_size(wl)
+
+    patterns = None
+    if want_patterns:
+        # The three forms the method is reshaped into, each against the plain FP32 form of this
+        # line on the same GPU, with its error stated.
+        patterns = {"plain_fp32": {"value": value, "unit": UNIT, "ms_per_step": ms / args.steps,
+                                   "error_vs_oracle": err}}
+        rp = []
+        for k, prec in enumerate(("fp16", "bf16")):
+            m = time_storage(wl, prec, args.steps, args.warmup, stream)
+            m["error_vs_oracle"] = errs[1 + k] if len(errs) > 1 + k else None
+            m["vs_plain_fp32"] = m["value"] / value
+            rp.append(m)
+        patterns["reduced_precision"] = rp
+        ens = measure_ensemble(args.precision, args.steps, args.warmup, rank=0, world=1, with_e2e=False)
+        patterns["batched_ensemble"] = {
+            "workload": ens["config"]["workload"], "value": ens["value"], "unit": UNIT,
+            "ms_per_step": ens["ms_per_step"], "separate_contexts": ens["separate_launches"],
+            "vs_separate_contexts": ens["speedup_vs_separate"],
+            "sweep_roofline_frac": ens["roofline"]["frac"],
+            "error": "bitwise identical to the same cells stepped as separate FP32 contexts; their error "
+                     "against the oracle is the FP32 storage error of plain_fp32"}
+        ntr, nte = args.pattern_closure_cells
+        clo = measure_closure(ntr, nte)
+        patterns["learned_closure"] = {
+            "workload": clo["config"]["workload"], "value": clo["value"], "unit": clo["unit"],
+            "drag_error_vs_fine": clo["drag_error_vs_fine"], "fine_method": clo["fine_method"],
+            "speedup_vs_fine_at_drag_accuracy": clo["speedup_vs_fine_at_drag_accuracy"],
+            "train_samples": clo["config"]["train_samples"], "test_samples": clo["config"]["test_samples"],
+            "seconds": {"generation": clo["generation_seconds"], "training": clo["training_seconds"]}}
 
     if rank == 0:
         solid = len(r) * (4.0 / 3.0 * math.pi * wl.radius ** 3) / N if lattice == 1 else None
@@ -425,9 +517,69 @@ def run_ours(args):
             "gpu_launches": int(info["launches_per_step"]) * args.steps,
             "clocks": clk,
         }
+        if patterns is not None:
+            line["patterns"] = patterns
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def time_storage(wl, precision, steps, warmup, stream):
+    """The headline workload in another storage precision (its default sweep kernel): whole-step
+    time with CUDA events over `steps` graph replays, and the sweep's per-launch time."""
+    import torch
+    from paper_1105_2904_gb300 import lbmp
+
+    lattice = 1 if wl.lattice == "D3Q19" else 0
+    nx, ny, nz = wl.dims
+    c, r, d, v = wl.particles()
+    sim = lbmp.Simulation(lattice, nx, ny, nz, wl.tau, body_force=wl.body_force, precision=precision,
+                          walls=wl.walls, gravity=wl.gravity, gap=0.0,
+                          body_force_on_particles=wl.body_force_on_particles, cuda_stream=stream.cuda_stream)
+    sim.add_particles(c, r, d, v)
+    sim.step(warmup)
+    sim.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sim.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = sim.profile(2 * min(max(steps // 2, 1), 25))
+    sim.close()
+    Q = 19 if lattice == 1 else 9
+    algo = 2 * Q * 2 * wl.sites
+    peak, _ = measured_peaks()
+    return {"storage": precision + " scaled deviations", "value": wl.sites * steps / (ms / 1e3) / 1e6,
+            "unit": UNIT, "ms_per_step": ms / steps, "sweep_ms": prof["sweep_ms"],
+            "particle_phase_ms": prof["particle_ms"],
+            "sweep_roofline_frac": algo / (prof["sweep_ms"] / 1e3) / 1e9 / peak,
+            "kernel": "k_sweep2 (two sites per thread, 16 threads along x)"}
+
+
+def cpu_full_size(wl):
+    """The all-core oracle on the full-size workload: set-up, then 10 steps timed; the per-step
+    time is what a full run of the oracle would take per step (extrapolated, not run)."""
+    import oracle as O
+
+    c, r, d, v = wl.particles()
+    nx, ny, nz = wl.dims
+    t = time.perf_counter()
+    sim = O.OracleSim(O.D3Q19, nx, ny, nz, wl.tau, body_force=wl.body_force,
+                      body_force_on_particles=wl.body_force_on_particles, openmp=True)
+    sim.add_particles(c, r, d, v)
+    setup = time.perf_counter() - t
+    t = time.perf_counter()
+    sim.step(10)
+    dt = time.perf_counter() - t
+    del sim
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": wl.sites * 10 / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%s, full size, 10 steps after %.1f s of set-up, FP64 C with OpenMP over the site "
+                      "loops; %.2f s per step, so %.0f s for the workload's %d steps (extrapolated)"
+                      % (wl.name, setup, dt / 10, dt / 10 * wl.steps, wl.steps)}
 
 
 def run_ensemble(args):
@@ -443,17 +595,27 @@ def run_ensemble(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    line = measure_ensemble(args.precision, args.steps, args.warmup, rank, world, with_e2e=not args.no_e2e)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_ensemble(prec, steps, warmup, rank, world, with_e2e=True):
+    """The ensemble measurement of run_ensemble; returns its JSON line (rank 0) or None."""
+    import torch
     from paper_1105_2904_gb300 import autotune as AT
     from paper_1105_2904_gb300 import build as B
     from paper_1105_2904_gb300 import lbmp
 
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     B.build()
     # Ensembles shard by cell: every rank advances its own 64 seeded cells (rank 0 the
     # reference ensemble), with no exchange between ranks.
     e = W.ensemble_cells(seed=4 + rank)
     n_cells = len(e.dims)
     F = [e.body_force] * n_cells
-    prec = args.precision
 
     def make_batch(p):
         b = lbmp.Batch(1, e.dims, e.taus, F, precision=p, gap=0.0, body_force_on_particles=e.body_force_on_particles)
@@ -467,10 +629,10 @@ def run_ensemble(args):
             torch.distributed.barrier()
 
     b = make_batch(prec)
-    spg = max(1, min(50, args.steps))
+    spg = max(1, min(50, steps))
     best, trials = AT.tune(b, trial_steps=8, steps_per_graph=spg)
     stream = torch.cuda.ExternalStream(b.stream)
-    b.step(args.warmup)
+    b.step(warmup)
     b.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -480,15 +642,15 @@ def run_ensemble(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    b.step(args.steps)
+    b.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     b.synchronize()
     info = b.info()
-    value, ms = aggregate_throughput(e.sites, args.steps, e0.elapsed_time(e1))
-    prof = b.profile(min(args.steps, 30))
+    value, ms = aggregate_throughput(e.sites, steps, e0.elapsed_time(e1))
+    prof = b.profile(min(steps, 30))
     bytes_per_site = {"fp32": 152, "fp16": 76, "bf16": 76, "fp64": 304}[prec]
     algo_bytes = bytes_per_site * e.sites
     peak, peak_kind = measured_peaks()
@@ -512,14 +674,14 @@ def run_ensemble(args):
         if len(e.radii[k]):
             s_.add_particles(e.centers[k], e.radii[k], e.densities[k], e.velocities[k])
         sims.append(s_)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         for s_ in sims:
             s_.step(1)
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(sep_stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for s_ in sims:
             s_.step(1)
     f1.record(sep_stream)
@@ -527,12 +689,12 @@ def run_ensemble(args):
     sep_ms = f0.elapsed_time(f1)
     for s_ in sims:
         s_.close()
-    sep_value, _ = aggregate_throughput(e.sites, args.steps, sep_ms)
+    sep_value, _ = aggregate_throughput(e.sites, steps, sep_ms)
 
     # End to end through the C-ABI with host buffers: batch creation, particle upload, then
     # every step a read-back of every cell's particle state.
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         torch.cuda.synchronize()
         t = time.perf_counter()
         b2 = make_batch(prec)
@@ -540,7 +702,7 @@ def run_ensemble(args):
         views = [b2.cell(k) for k in range(n_cells)]
         hosts = [{q: np.empty((len(e.radii[k]), 3)) for q in ("x", "u", "omega", "force", "torque")}
                  for k in range(n_cells)]
-        for _ in range(args.steps):
+        for _ in range(steps):
             b2.step(1)
             for k in range(n_cells):
                 if len(e.radii[k]):
@@ -549,16 +711,16 @@ def run_ensemble(args):
         b2.close()
         dt = reduce_max(dt)
         h2d = sum(c.nbytes + r.nbytes + d.nbytes + v.nbytes
-                  for c, r, d, v in zip(e.centers, e.radii, e.densities, e.velocities)) / args.steps
-        e2e = {"value": reduce_sum(e.sites) * args.steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                  for c, r, d, v in zip(e.centers, e.radii, e.densities, e.velocities)) / steps
+        e2e = {"value": reduce_sum(e.sites) * steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(5 * 3 * 8 * e.n_particles),
                "includes": "batch creation, particle upload and site classification, %d steps each followed "
-                           "by a particle-state read-back of every cell" % args.steps}
+                           "by a particle-state read-back of every cell" % steps}
 
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        return {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": e.name, "cells": n_cells, "sites": e.sites, "total_cells": n_cells * world, "particles": e.n_particles,
@@ -567,7 +729,7 @@ def run_ensemble(args):
                                   "steps_per_graph": spg, "candidates": len(trials)},
                        "parallelism": ("cells sharded: %d distinct seeded cells per GPU" % n_cells) if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GB of distributions per step" % (algo_bytes / 1e9)},
-            "separate_launches": {"value": sep_value, "unit": UNIT, "ms_per_step": sep_ms / args.steps,
+            "separate_launches": {"value": sep_value, "unit": UNIT, "ms_per_step": sep_ms / steps,
                                   "launches_per_step": "one step graph per cell (%d)" % n_cells,
                                   "error": ("bitwise identical to the batch (FP32 contexts default to the one-site "
                                             "sweep, the batch's kernel)" if prec in ("fp32", "fp64") else
@@ -575,12 +737,10 @@ def run_ensemble(args):
                                             "agree with the batch to storage rounding")},
             "speedup_vs_separate": value / sep_value,
             "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
-            "gpu_launches": int(info["launches_per_step"]) * args.steps,
+            "gpu_launches": int(info["launches_per_step"]) * steps,
             "clocks": clk,
         }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return None
 
 
 def run_closure(args):
@@ -596,12 +756,21 @@ def run_closure(args):
     if world > 1 and rank != 0:
         return
     torch.cuda.set_device(local)
+    ntr, nte = args.closure_cells
+    print(json.dumps(measure_closure(ntr, nte, args.closure_large_cells)), flush=True)
+
+
+def measure_closure(ntr, nte, n_large=0):
+    """The closure measurement of run_closure on ntr training and nte held-out cells; returns
+    its JSON line. n_large > 0: the trained network is also judged on that many held-out
+    cells of the large configuration (128^3 coarse cells with 200 spheres of radius 3, 512^3
+    fine twins with radius 12; 1.1 % solid against the training cells' 2.8 %)."""
+    import torch
     from paper_1105_2904_gb300 import build as B
     from paper_1105_2904_gb300 import closure as CL
 
     B.build()
     spec = CL.PairSpec()
-    ntr, nte = args.closure_cells
     t0 = time.perf_counter()
     Xtr, Ttr, ctr, ftr, str_ = CL.generate(spec, ntr, seed=1)
     t_gen = time.perf_counter() - t0
@@ -654,8 +823,24 @@ def run_closure(args):
             "closure_path_seconds": {"coarse_runs": t_c, "inference": t_inf},
             "speedup_vs_fine_at_drag_accuracy": t_f / (t_c + t_inf),
             "generation_seconds": t_gen, "training_seconds": t_train}
-    print(json.dumps(line), flush=True)
+    if n_large > 0:
+        big = CL.PairSpec(L=128, n_spheres=200)
+        t0 = time.perf_counter()
+        Xb, Tb, cb, fb, sb = CL.generate(big, n_large, seed=3)
+        t_big = time.perf_counter() - t0
+        eb_coarse = CL.drag_errors(cb, fb)
+        eb_closure = CL.drag_errors(cl.corrected(Xb, cb, sb), fb)
+        line["large_cells"] = {
+            "workload": "128^3 coarse cells, 200 spheres r=3 (512^3 fine twins, r=12), held-out seeds",
+            "cells": n_large, "samples": int(Xb.shape[0]),
+            "drag_error_vs_fine": {"coarse_mean": float(eb_coarse.mean()),
+                                   "coarse_p95": float(np.percentile(eb_coarse, 95)),
+                                   "closure_mean": float(eb_closure.mean()),
+                                   "closure_p95": float(np.percentile(eb_closure, 95))},
+            "trained_on": "the %d small cells above (32^3, 8 spheres each)" % ntr,
+            "generation_seconds": t_big}
     cl.close()
+    return line
 
 
 def main():

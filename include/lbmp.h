@@ -151,6 +151,17 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, double* rho, double* u);
 lbm_status lbm_get_particles(lbm_ctx* ctx, double* x, double* u, double* omega,
                              double* force, double* torque);
 
+/* Orientation of each particle after the last step, q[n*4]: the unit quaternion (w, x, y, z)
+ * of the rotation from the particle's attitude when it was added (the identity) to its
+ * attitude now. It is the angular part of the rigid-body integration (Sec. 2.2: the particle
+ * moves with the velocities Eqs. 10-11 give, Eq. 13 for the position): every step the
+ * quaternion is turned by |omega| about omega, omega the angular velocity after that step's
+ * acceleration (space frame, held over dt = 1), q <- dq q with dq = (cos(|omega|/2),
+ * sin(|omega|/2) omega/|omega|), and renormalised; FP64 on the device in every storage
+ * precision. The spheres' dynamics do not depend on it. Synchronizes.
+ * LBM_E_INVALID for a NULL argument. */
+lbm_status lbm_get_orientations(lbm_ctx* ctx, double* q);
+
 /* Asynchronous form of lbm_get_particles (the same quantities, Eqs. 8-9 and 10-13; the
  * asynchrony has no counterpart in the paper) for loops that read the particles every step
  * without stalling the device: enqueues on the context's stream, after the work so far, the

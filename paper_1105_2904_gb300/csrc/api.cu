@@ -163,6 +163,7 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     a.tmpl = ctx->tmpl;
     a.tag = ctx->tag;
     a.x = ctx->x;
+    a.q = ctx->q;
     a.Kold = ctx->Kold;
     a.un = ctx->un;
     a.acc = ctx->acc;
@@ -274,9 +275,13 @@ int enqueue_step(lbm_ctx* ctx, int c, cudaEvent_t* ev = nullptr)
 {
     const SweepArgs a = sweep_args(ctx, c);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
-    ctx->kt->sweep(a, ctx->stream);
+    {
+        NvtxRange r("lbm sweep");
+        ctx->kt->sweep(a, ctx->stream);
+    }
     if (ev) cudaEventRecord(ev[1], ctx->stream);
     int launches = 1;
+    NvtxRange rp("lbm particle phase");
     if (ctx->np > 0) {
         const ParticleArgs pa = particle_args(ctx);
         const ISFixArgs fa = is_fix_args(ctx, c);
@@ -613,6 +618,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     ctx->h_pk.insert(ctx->h_pk.end(), pk.begin(), pk.end());
     ctx->h_pkf.insert(ctx->h_pkf.end(), pkf.begin(), pkf.end());
     ctx->h_x.insert(ctx->h_x.end(), xs.begin(), xs.end());
+    for (int q = 0; q < n; ++q) ctx->h_q.insert(ctx->h_q.end(), {1.0, 0.0, 0.0, 0.0});
     const int first = ctx->np;
     ctx->np = tot;
 
@@ -629,7 +635,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
         }
         cudaFree(p);
     };
-    for (void* p : {(void*)ctx->pk, (void*)ctx->pkf, (void*)ctx->pk_prev, (void*)ctx->pkf_prev, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->un,
+    for (void* p : {(void*)ctx->pk, (void*)ctx->pkf, (void*)ctx->pk_prev, (void*)ctx->pkf_prev, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->q, (void*)ctx->un,
                     (void*)ctx->acc, (void*)ctx->force, (void*)ctx->Kold, (void*)ctx->cell_of,
                     (void*)ctx->cell_count, (void*)ctx->cell_start, (void*)ctx->cell_cursor,
                     (void*)ctx->cell_items, (void*)ctx->changed, (void*)ctx->restamp,
@@ -643,6 +649,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CS(dev_alloc(ctx, &ctx->pc, sizeof(PConst) * np));
     CS(dev_alloc(ctx, &ctx->tmpl, sizeof(int) * ctx->h_tmpl.size()));
     CS(dev_alloc(ctx, &ctx->x, sizeof(double) * 3 * np));
+    CS(dev_alloc(ctx, &ctx->q, sizeof(double) * 4 * np));
     CS(dev_alloc(ctx, &ctx->un, sizeof(double) * 3 * np));
     CS(dev_alloc(ctx, &ctx->acc, sizeof(double) * 6 * np));
     CS(dev_alloc(ctx, &ctx->force, sizeof(double) * 6 * np));
@@ -685,6 +692,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CK(cudaMemcpyAsync(ctx->tmpl, ctx->h_tmpl.data(), sizeof(int) * ctx->h_tmpl.size(), cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaMemcpyAsync(ctx->x, ctx->h_x.data(), sizeof(double) * 3 * np, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->q, ctx->h_q.data(), sizeof(double) * 4 * np, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 6 * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->force, 0, sizeof(double) * 6 * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->tag, 0xFF, sizeof(unsigned) * (size_t)ctx->g.N, ctx->stream));
@@ -709,6 +717,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int n)
     CS(ensure_alloc(ctx));
     CS(build_graphs(ctx));
     ctx->stepped = true;
+    NvtxRange r("lbm_step");
     for (int s = 0; s < n; ++s) {
         CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream));
         ctx->cur ^= 1;
@@ -927,6 +936,25 @@ lbm_status lbm_get_particles(lbm_ctx* ctx, double* x, double* u, double* omega, 
     double* outs[5] = {x, u, omega, force, torque};
     for (int k = 0; k < 5; ++k)
         if (outs[k]) std::memcpy(outs[k], h + (size_t)k * 3 * np, sizeof(double) * 3 * np);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_orientations(lbm_ctx* ctx, double* q)
+{
+    if (!ctx || !q) return LBM_E_INVALID;
+    const size_t np = (size_t)ctx->np;
+    if (np == 0) return sync_status(ctx);
+    const size_t bytes = sizeof(double) * 4 * np;
+    if (ctx->pinned_bytes < bytes) {
+        if (ctx->pinned) cudaFreeHost(ctx->pinned);
+        ctx->pinned = nullptr;
+        ctx->pinned_bytes = 0;
+        CK(cudaMallocHost(&ctx->pinned, bytes));
+        ctx->pinned_bytes = bytes;
+    }
+    CK(cudaMemcpyAsync(ctx->pinned, ctx->q, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CS(sync_status(ctx));
+    std::memcpy(q, ctx->pinned, bytes);
     return LBM_OK;
 }
 

@@ -413,6 +413,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n)
     BS(build(b));
     BS(same_parity(b));
     const int K = b->steps_per_graph;
+    NvtxRange r("lbm_batch_step");
     while (n > 0) {
         const int cur = b->cells[0]->cur;
         if (K > 1 && n >= K) {

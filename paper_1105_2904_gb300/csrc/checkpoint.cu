@@ -2,7 +2,7 @@
 //
 // A checkpoint is the state at a step boundary: the distribution buffer the next sweep reads
 // (in the storage format, IS sites carrying their density), the owner map and the IS-source
-// masks, the particles' kinematic records, positions and last forces, the pending-imposition
+// masks, the particles' kinematic records, positions, orientations and last forces, the pending-imposition
 // flag, the step stamp of the boundary-site records and the wall velocities; with in-place
 // streaming also the layout parity and the IS-site densities the next sweep reads. Everything else
 // a step uses is rebuilt inside the step. The constant part of the set-up (lattice, sizes,
@@ -19,7 +19,7 @@ using namespace lbmp::host;
 namespace {
 
 constexpr char kMagic[8] = {'L', 'B', 'M', 'P', 'C', 'K', 'P', '1'};
-constexpr int kVersion = 3;
+constexpr int kVersion = 4;
 
 struct CkptHeader {
     char magic[8];
@@ -99,6 +99,7 @@ std::vector<Section> sections(lbm_ctx* ctx)
         s.push_back({ctx->pk, sizeof(PKern) * np});
         s.push_back({ctx->pkf, sizeof(PKernF) * np});
         s.push_back({ctx->x, sizeof(double) * 3 * np});
+        s.push_back({ctx->q, sizeof(double) * 4 * np});
         s.push_back({ctx->force, sizeof(double) * 6 * np});
     }
     s.push_back({ctx->pending, sizeof(int)});

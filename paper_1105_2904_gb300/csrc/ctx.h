@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 #include "lbmp.h"
 
@@ -53,6 +55,7 @@ struct lbm_ctx {
     std::vector<lbmp::PKern> h_pk;
     std::vector<lbmp::PKernF> h_pkf;
     std::vector<double> h_x;
+    std::vector<double> h_q;   // orientations (w, x, y, z) when added: the identity
     std::vector<int> h_tmpl;
     lbmp::PKern* pk = nullptr;
     lbmp::PKernF* pkf = nullptr;
@@ -61,6 +64,7 @@ struct lbm_ctx {
     lbmp::PConst* pc = nullptr;
     int* tmpl = nullptr;
     double *x = nullptr, *un = nullptr, *acc = nullptr, *force = nullptr;
+    double* q = nullptr;       // [np][4] orientation quaternions (w, x, y, z)
     int* Kold = nullptr;
     lbmp::Counters* cnt = nullptr;
     int* status = nullptr;
@@ -95,6 +99,16 @@ struct lbm_ctx {
 
 namespace lbmp {
 namespace host {
+
+// NVTX range for the duration of a scope: names the host-side enqueue of a step and of its
+// kernel groups (sweep, particle phase) in a profiler's timeline. Header-only NVTX: without a
+// tool attached the calls return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 inline lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg)
 {

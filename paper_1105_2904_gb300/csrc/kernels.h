@@ -171,6 +171,7 @@ struct ParticleArgs {
     const int* tmpl;
     unsigned* tag;
     double* x;          // [np][3] centres
+    double* q;          // [np][4] orientations, unit quaternions (w, x, y, z)
     int* Kold;          // [np][3] anchor before this step's move
     double* un;         // [np][3] velocity during the contact step
     double* acc;        // [np][6]

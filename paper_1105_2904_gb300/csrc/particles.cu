@@ -158,18 +158,24 @@ __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a0, cons
     }
 }
 
+// Contact-grid cell of a centre coordinate. FP32 is enough: the cell only selects which
+// pairs are tested (the tests themselves are FP64), and cells are at least 2 r_max + gap + 4
+// wide, two sites more than the widest reach of a pair within one step, which absorbs the
+// FP32 rounding of the coordinate by orders of magnitude (GB300's FP64 pipe is narrow, and
+// the FP64 divisions here dominated the kernel).
 __device__ inline int cell_coord(const ParticleArgs& a, int k, double x)
 {
     const int n = axis_len(a.g, k);
     const int D = a.lattice == 0 ? 2 : 3;
     if (k >= D) return 0;
-    double v;
+    float v;
+    const float xf = (float)x;
     if (a.g.wall[k]) {
-        v = x + 0.5;
+        v = xf + 0.5f;
     } else {
-        v = x - (double)n * floor(x / (double)n);
+        v = xf - (float)n * floorf(xf / (float)n);
     }
-    int c = (int)floor(v / a.cg.size[k]);
+    int c = (int)floorf(v / (float)a.cg.size[k]);
     if (c < 0) c = 0;
     if (c >= a.cg.n[k]) c = a.cg.n[k] - 1;
     return c;
@@ -370,6 +376,27 @@ __global__ void k_resolve(const ParticleArgs a0, const ParticleArgs* __restrict_
     }
 }
 
+// Orientation of a particle after one step (the rigid-body integration of Sec. 2.2, beside
+// Eq. 13 for the position): the unit quaternion q = (w, x, y, z) turned by theta = |omega|
+// about omega / |omega| (space frame), omega the angular velocity after this step's
+// acceleration (Eq. 11) held over dt = 1: q' = dq q, dq = (cos(theta/2), sin(theta/2)
+// omega/|omega|), then divided by its norm. FP64, evaluated as written (-fmad=false).
+__device__ void rotate_orientation(double* q, const double om[3])
+{
+    const double th = sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
+    if (th == 0.0) return;
+    const double c = cos(0.5 * th), sn = sin(0.5 * th) / th;
+    const double d[4] = {c, sn * om[0], sn * om[1], sn * om[2]};
+    const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+    double r[4];
+    r[0] = d[0] * q0 - (d[1] * q1 + d[2] * q2 + d[3] * q3);
+    r[1] = d[0] * q1 + q0 * d[1] + (d[2] * q3 - d[3] * q2);
+    r[2] = d[0] * q2 + q0 * d[2] + (d[3] * q1 - d[1] * q3);
+    r[3] = d[0] * q3 + q0 * d[3] + (d[1] * q2 - d[2] * q1);
+    const double nrm = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    for (int k = 0; k < 4; ++k) q[k] = r[k] / nrm;
+}
+
 // Walls, position update (Eq. 13), new shifts (Eqs. 14-15) and the list of particles whose
 // shift changed; one thread per particle.
 template <bool B>
@@ -415,6 +442,7 @@ __global__ void k_move(const ParticleArgs a0, const ParticleArgs* __restrict__ c
             const int n = axis_len(a.g, q);
             k.Kw[q] = a.g.wall[q] ? Kn : ((Kn % n) + n) % n;
         }
+        rotate_orientation(&a.q[(size_t)p * 4], k.om);
         PKernF& kf = a.pkf[p];
         for (int q = 0; q < 3; ++q) {
             kf.u[q] = (float)k.u[q];
@@ -562,7 +590,7 @@ int particle_phase_a(const ParticleArgs& a0, const ParticleArgs* cells, const Ph
     k_resolve<B><<<dim3(1, nc), rthreads, smem, s>>>(a0, cells);
     k_move<B><<<gp, PT, 0, s>>>(a0, cells);
     k_mark_neighbours<B><<<gp, PT, 0, s>>>(a0, cells);
-    return 10;
+    return 9;
 }
 
 template <bool B>

@@ -165,7 +165,19 @@ __device__ __forceinline__ void collide_plain(double f[], const SweepArgs& a)
 //   g*_i = (1 - omega) g_i + A + B,  g*_opp(i) = (1 - omega) g_opp(i) + A - B,
 //   A = omega w (drho + rho (4.5 (c.u)^2 - 1.5 u^2)) + pre w (9 (c.u)(c.F) - 3 u.F),
 //   B = 3 omega w rho (c.u) + 3 pre w (c.F).
-template <class L>
+//
+// CONSERVE (FP32 storage): the momentum the collision hands the stored populations is made
+// exact. In exact arithmetic the increments g*_i - g_i carry momentum F (Eq. 3 conserves
+// rho u and the Guo term adds F). In FP32 the equilibrium, evaluated at the magnitude of g,
+// is off by a few units in the last place, and in a slowly changing flow those errors repeat
+// step after step with the same sign: the momentum drifts (after 1000 steps of a
+// body-force-driven suspension, by ~1e-4 of the velocity). Here the increments as stored are
+// taken back, g*_i - g_i (exact when g*_i and g_i are within a factor of two, as they are
+// near equilibrium), their momentum S = sum_i c_i (g*_i - g_i) is compared with F, and the
+// axis pair of each direction k absorbs (F_k - S_k) / 2 with opposite signs. What is left is
+// one rounding of that correction per axis population, which varies from step to step and
+// does not accumulate.
+template <class L, bool CONSERVE = false>
 __device__ __forceinline__ void collide_dev(float g[], const SweepArgs& a, float& drho, float& j0, float& j1,
                                             float& j2)
 {
@@ -188,24 +200,63 @@ __device__ __forceinline__ void collide_dev(float g[], const SweepArgs& a, float
     const float omega = a.omega_f, pre = a.pre_f, om1 = 1.0f - omega;
     const float uF3 = 3.0f * (u[0] * F0 + u[1] * F1 + u[2] * F2);
     const float usq15 = 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    {   // rest direction
-        const float w = (float)L::w(0);
-        g[0] = om1 * g[0] + omega * w * (drho - rho * usq15) - pre * w * uF3;
-    }
-    sfor<1, Q>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        constexpr int j = L::opp(i);
-        if constexpr (j > i) {
-            const float cu = (float)L::c(i, 0) * u[0] + (float)L::c(i, 1) * u[1] + (float)L::c(i, 2) * u[2];
-            const float cF = (float)L::c(i, 0) * F0 + (float)L::c(i, 1) * F1 + (float)L::c(i, 2) * F2;
-            const float w = (float)L::w(i);
-            const float ow = omega * w, pw = pre * w;
-            const float A = ow * (drho + rho * (4.5f * cu * cu - usq15)) + pw * (9.0f * cu * cF - uF3);
-            const float B = 3.0f * (ow * rho * cu + pw * cF);
-            g[i] = om1 * g[i] + (A + B);
-            g[j] = om1 * g[j] + (A - B);
+    if constexpr (!CONSERVE) {
+        {   // rest direction
+            const float w = (float)L::w(0);
+            g[0] = om1 * g[0] + omega * w * (drho - rho * usq15) - pre * w * uF3;
         }
-    });
+        sfor<1, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int j = L::opp(i);
+            if constexpr (j > i) {
+                const float cu = (float)L::c(i, 0) * u[0] + (float)L::c(i, 1) * u[1] + (float)L::c(i, 2) * u[2];
+                const float cF = (float)L::c(i, 0) * F0 + (float)L::c(i, 1) * F1 + (float)L::c(i, 2) * F2;
+                const float w = (float)L::w(i);
+                const float ow = omega * w, pw = pre * w;
+                const float A = ow * (drho + rho * (4.5f * cu * cu - usq15)) + pw * (9.0f * cu * cF - uF3);
+                const float B = 3.0f * (ow * rho * cu + pw * cF);
+                g[i] = om1 * g[i] + (A + B);
+                g[j] = om1 * g[j] + (A - B);
+            }
+        });
+    } else {
+        {   // rest direction (no momentum)
+            const float w = (float)L::w(0);
+            g[0] = om1 * g[0] + omega * w * (drho - rho * usq15) - pre * w * uF3;
+        }
+        float S[3] = {0.0f, 0.0f, 0.0f};  // momentum of the stored increments
+        sfor<1, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int j = L::opp(i);
+            if constexpr (j > i) {
+                constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+                const float cu = (float)cx * u[0] + (float)cy * u[1] + (float)cz * u[2];
+                const float cF = (float)cx * F0 + (float)cy * F1 + (float)cz * F2;
+                const float w = (float)L::w(i);
+                const float ow = omega * w, pw = pre * w;
+                const float A = ow * (drho + rho * (4.5f * cu * cu - usq15)) + pw * (9.0f * cu * cF - uF3);
+                const float B = 3.0f * (ow * rho * cu + pw * cF);
+                const float gi = om1 * g[i] + (A + B);
+                const float gj = om1 * g[j] + (A - B);
+                const float d = (gi - g[i]) - (gj - g[j]);  // c_j = -c_i
+                if constexpr (cx != 0) S[0] += (float)cx * d;
+                if constexpr (cy != 0) S[1] += (float)cy * d;
+                if constexpr (cz != 0) S[2] += (float)cz * d;
+                g[i] = gi;
+                g[j] = gj;
+            }
+        });
+        const float Fk[3] = {F0, F1, F2};
+        sfor<1, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+            if constexpr (cx * cx + cy * cy + cz * cz == 1) {
+                constexpr int axis = cx != 0 ? 0 : (cy != 0 ? 1 : 2);
+                const float half = 0.5f * (Fk[axis] - S[axis]);
+                g[i] = (cx + cy + cz) > 0 ? g[i] + half : g[i] - half;
+            }
+        });
+    }
 }
 
 // All equilibrium deviations g^eq_i(drho, u) (FP32), by opposite pairs.
@@ -646,7 +697,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
 
     float mrho = 0.f, mj0 = 0.f, mj1 = 0.f, mj2 = 0.f;  // pre-collision moments (FP32 path)
     if constexpr (St::deviation)
-        collide_dev<L>(f, a, mrho, mj0, mj1, mj2);
+        collide_dev<L, std::is_same<S, float>::value>(f, a, mrho, mj0, mj1, mj2);
     else
         collide_plain<L>(f, a);
 

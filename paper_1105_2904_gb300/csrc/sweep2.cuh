@@ -106,8 +106,9 @@ __device__ __forceinline__ void pull2(const S* __restrict__ fin, const Geom& g, 
 }
 
 // BGK collision with Guo forcing (Eq. 3) of both sites on packed pairs; the same expression
-// as collide_dev, one instruction for two sites.
-template <class L>
+// as collide_dev, one instruction for two sites (CONSERVE: the stored increments' momentum is
+// made exact, as collide_dev<L, true> describes).
+template <class L, bool CONSERVE = false>
 __device__ __forceinline__ void collide_dev2(float2 g[], const SweepArgs& a, float2& drho, float2& j0, float2& j1,
                                              float2& j2)
 {
@@ -133,6 +134,7 @@ __device__ __forceinline__ void collide_dev2(float2 g[], const SweepArgs& a, flo
     const float omega = a.omega_f, pre = a.pre_f, om1 = 1.0f - omega;
     const float2 uF3 = mul2(p2(3.0f), fma2(u2, p2(F2), fma2(u1, p2(F1), mul2(u0, p2(F0)))));
     const float2 usq15 = mul2(p2(1.5f), fma2(u2, u2, fma2(u1, u1, mul2(u0, u0))));
+    float2 S[3] = {p2(0.0f), p2(0.0f), p2(0.0f)};  // CONSERVE: momentum of the stored increments
     {   // rest direction
         const float w = (float)L::w(0);
         const float2 e = fma2(rho, mul2(usq15, p2(-1.0f)), drho);  // drho - rho usq15
@@ -165,10 +167,33 @@ __device__ __forceinline__ void collide_dev2(float2 g[], const SweepArgs& a, flo
             const float2 A = fma2(p2(ow), fma2(rho, q, drho), mul2(p2(pw), fma2(cu, p2(9.0f * cF), mul2(uF3, p2(-1.0f)))));
             // B = 3 (ow rho cu + pw cF)
             const float2 B = mul2(p2(3.0f), fma2(mul2(p2(ow), rho), cu, p2(pw * cF)));
-            g[i] = fma2(p2(om1), g[i], add2(A, B));
-            g[j] = fma2(p2(om1), g[j], sub2(A, B));
+            const float2 gi = fma2(p2(om1), g[i], add2(A, B));
+            const float2 gj = fma2(p2(om1), g[j], sub2(A, B));
+            if constexpr (CONSERVE) {
+                const float2 d = sub2(sub2(gi, g[i]), sub2(gj, g[j]));  // c_j = -c_i
+                if constexpr (cx > 0) S[0] = add2(S[0], d);
+                if constexpr (cx < 0) S[0] = sub2(S[0], d);
+                if constexpr (cy > 0) S[1] = add2(S[1], d);
+                if constexpr (cy < 0) S[1] = sub2(S[1], d);
+                if constexpr (cz > 0) S[2] = add2(S[2], d);
+                if constexpr (cz < 0) S[2] = sub2(S[2], d);
+            }
+            g[i] = gi;
+            g[j] = gj;
         }
     });
+    if constexpr (CONSERVE) {
+        const float Fk[3] = {F0, F1, F2};
+        sfor<1, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+            if constexpr (cx * cx + cy * cy + cz * cz == 1) {
+                constexpr int axis = cx != 0 ? 0 : (cy != 0 ? 1 : 2);
+                const float2 half = mul2(p2(0.5f), sub2(p2(Fk[axis]), S[axis]));
+                g[i] = (cx + cy + cz) > 0 ? add2(g[i], half) : sub2(g[i], half);
+            }
+        });
+    }
 }
 
 // Lever arms of both sites (each from its own owner's record) as pairs.
@@ -418,7 +443,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep2(const SweepArgs a)
         }
     }
     float2 mrho, mj0, mj1, mj2;
-    collide_dev2<L>(f, a, mrho, mj0, mj1, mj2);
+    collide_dev2<L, std::is_same<S, float>::value>(f, a, mrho, mj0, mj1, mj2);
     bool any_is = false;
     bool is0 = false, is1 = false;
     if constexpr (PART) {

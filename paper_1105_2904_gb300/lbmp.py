@@ -26,7 +26,8 @@ LBM_STREAM_PULL, LBM_STREAM_INPLACE = 0, 1
 STREAMING = {"pull": LBM_STREAM_PULL, "inplace": LBM_STREAM_INPLACE}
 
 EXPORTED = ("lbm_create", "lbm_configure", "lbm_set_wall_velocity", "lbm_add_particles", "lbm_step", "lbm_synchronize",
-            "lbm_get_fields", "lbm_get_particles", "lbm_get_distributions", "lbm_set_distributions",
+            "lbm_get_fields", "lbm_get_particles", "lbm_get_orientations", "lbm_get_distributions",
+            "lbm_set_distributions",
             "lbm_get_masks", "lbm_get_info", "lbm_profile_steps", "lbm_set_sweep_shape", "lbm_set_streaming", "lbm_diagnostics",
             "lbm_bs_exchange_noalloc",
             "lbm_checkpoint_size", "lbm_checkpoint_save", "lbm_checkpoint_load", "lbm_get_particles_async",
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_synchronize.argtypes = [P]
     lib.lbm_get_fields.argtypes = [P, D, D]
     lib.lbm_get_particles.argtypes = [P, D, D, D, D, D]
+    lib.lbm_get_orientations.argtypes = [P, D]
     lib.lbm_get_distributions.argtypes = [P, D]
     lib.lbm_set_distributions.argtypes = [P, D]
     lib.lbm_get_masks.argtypes = [P, ctypes.POINTER(ctypes.c_uint)]
@@ -208,6 +210,12 @@ def lbm_get_particles(h, n, out=None):
     out = out or {k: np.empty((n, 3)) for k in ("x", "u", "omega", "force", "torque")}
     _check(h, load().lbm_get_particles(h, _dp(out["x"]), _dp(out["u"]), _dp(out["omega"]),
                                        _dp(out["force"]), _dp(out["torque"])))
+    return out
+
+
+def lbm_get_orientations(h, n, out=None):
+    out = np.empty((n, 4)) if out is None else out
+    _check(h, load().lbm_get_orientations(h, _dp(out)))
     return out
 
 
@@ -501,6 +509,10 @@ class Simulation:
 
     def get_particles(self):
         return lbm_get_particles(self.h, self.np)
+
+    def get_orientations(self):
+        """[np][4] unit quaternions (w, x, y, z) of the particles' attitudes (lbm_get_orientations)."""
+        return lbm_get_orientations(self.h, self.np)
 
     def get_particles_async(self, pinned):
         """Enqueues a read-back into `pinned` (a page-locked float64 torch tensor of 15 np + 1

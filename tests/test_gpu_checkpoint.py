@@ -34,7 +34,9 @@ def _setup(precision, radius=4.5):
 
 def _state(g):
     p = g.get_particles()
-    return g.get_f(), g.get_tags(), {k: p[k].copy() for k in ("x", "u", "omega", "force", "torque")}
+    d = {k: p[k].copy() for k in ("x", "u", "omega", "force", "torque")}
+    d["orientation"] = g.get_orientations()
+    return g.get_f(), g.get_tags(), d
 
 
 def _same(a, b):

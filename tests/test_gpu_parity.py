@@ -134,6 +134,11 @@ def test_suspension_fp64_matches_oracle_exactly(case):
     for k in ("x", "u", "omega", "force", "torque"):
         assert rel(pg[k], pr[k], max(np.max(np.abs(pr[k])), 1e-300)) <= 1e-12, k
     assert rel(g.get_f(), r.get_f()) <= 1e-12
+    # orientations: FP64 quaternion integration on both sides (cos / sin of the two math
+    # libraries may differ in the last place)
+    qg, qr = g.get_orientations(), r.get_orientations()
+    assert np.max(np.abs(qg - qr)) <= 1e-13
+    np.testing.assert_allclose((qg * qg).sum(1), 1.0, rtol=0, atol=1e-15)
 
 
 @pytest.mark.parametrize("case", PCASES, ids=[c["name"] for c in PCASES])
@@ -148,8 +153,13 @@ def test_suspension_fp32_within_tolerance(case):
     rad = np.asarray(case["particles"][1], dtype=float)
     tscale = max(np.max(np.abs(pr["torque"])), np.max(np.abs(pr["force"])) * rad.max())
     assert rel(pg["torque"], pr["torque"], tscale) <= 1e-4
-    # trajectories: relative to the particle radius
+    # trajectories: relative to the particle radius; orientations: the angle between them
     assert np.max(np.abs(pg["x"] - pr["x"]) / rad[:, None]) <= 1e-5
+    # (the angle between the two attitudes, against the angle |omega| sweeps over the run)
+    qg, qr = g.get_orientations(), r.get_orientations()
+    angle = 2.0 * np.arccos(np.clip(np.abs((qg * qr).sum(1)), 0.0, 1.0))
+    sweep = case["steps"] * np.max(np.linalg.norm(pr["omega"], axis=1))
+    assert np.max(angle) <= 1e-4 * sweep + 1e-7
 
 
 def test_contacts_happen_in_the_collision_cases():
