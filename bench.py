@@ -397,8 +397,8 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (prof["sweep_ms"] / 1e3) / 1e9
     # which sweep kernel ran: the two-site one for an explicit two-site shape, or by default for
-    # the 16-bit storages (lbm_set_sweep_shape), where nx is even
-    shape = args.sweep_shape if args.sweep_shape >= 0 else (16 if args.precision in ("fp16", "bf16") else 0)
+    # every deviation storage (lbm_set_sweep_shape), where nx is even
+    shape = args.sweep_shape if args.sweep_shape >= 0 else (0 if args.precision == "fp64" else 16)
     two_site = shape > 0 and args.precision != "fp64" and nx % 2 == 0 and args.streaming == "pull"
     inplace = args.streaming == "inplace"
     kernel_key = "%s_%s_%s" % ("sweep_inplace" if inplace else ("sweep2" if two_site else "sweep"),
@@ -671,6 +671,7 @@ def measure_ensemble(prec, steps, warmup, rank, world, with_e2e=True):
         nx, ny, nz = e.dims[k]
         s_ = lbmp.Simulation(1, nx, ny, nz, e.taus[k], body_force=e.body_force, precision=prec, gap=0.0,
                              body_force_on_particles=e.body_force_on_particles, cuda_stream=sep_stream.cuda_stream)
+        s_.set_sweep_shape(0)   # the batch sweep's kernel: results bit for bit those of the batch
         if len(e.radii[k]):
             s_.add_particles(e.centers[k], e.radii[k], e.densities[k], e.velocities[k])
         sims.append(s_)
@@ -731,10 +732,8 @@ def measure_ensemble(prec, steps, warmup, rank, world, with_e2e=True):
                        "l2": "inputs larger than L2: %.1f GB of distributions per step" % (algo_bytes / 1e9)},
             "separate_launches": {"value": sep_value, "unit": UNIT, "ms_per_step": sep_ms / steps,
                                   "launches_per_step": "one step graph per cell (%d)" % n_cells,
-                                  "error": ("bitwise identical to the batch (FP32 contexts default to the one-site "
-                                            "sweep, the batch's kernel)" if prec in ("fp32", "fp64") else
-                                            "same method; 16-bit contexts default to the two-site sweep, so results "
-                                            "agree with the batch to storage rounding")},
+                                  "error": "bitwise identical to the batch (the contexts run the one-site sweep, "
+                                           "the batch's kernel)"},
             "speedup_vs_separate": value / sep_value,
             "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
             "gpu_launches": int(info["launches_per_step"]) * steps,

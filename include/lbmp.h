@@ -54,7 +54,9 @@ typedef enum {
     LBM_E_STATE = 6,    /* call not allowed in the current state (e.g. configure after step) */
     LBM_E_NAN = 7,      /* non-finite value detected in the state */
     LBM_E_CAPACITY = 8, /* a device work list overflowed (e.g. contact pairs) */
-    LBM_E_UNSTABLE = 9  /* a particle moved by more than one site in one step */
+    LBM_E_UNSTABLE = 9, /* a particle moved by more than one site in one step */
+    LBM_E_BOUNDS = 10   /* only in the bounds-checked build (LBM_DEBUG): a kernel found an index
+                           out of range and skipped that access */
 } lbm_status;
 
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
@@ -216,9 +218,9 @@ lbm_status lbm_profile_steps(lbm_ctx* ctx, int n, double out_ms[3]);
  * selects the two-site kernel (each thread updates the sites x, x + 1 with paired 8- or
  * 4-byte accesses and packed FP32 pair arithmetic; blocks of 128 threads, threads_x of them
  * along x, 128 / threads_x rows); 0 selects the one-site kernel; -1 (the default) picks
- * the one-site kernel for FP32 storage and the two-site kernel with 16 threads along x for
- * FP16 / BF16 storage. FP64 storage always uses the one-site kernel. Drops the captured
- * step graphs. LBM_E_INVALID for other values. */
+ * the two-site kernel with 16 threads along x (the one-site kernel where nx is odd). FP64
+ * storage always uses the one-site kernel. Drops the captured step graphs. LBM_E_INVALID for
+ * other values. */
 lbm_status lbm_set_sweep_shape(lbm_ctx* ctx, int threads_x);
 
 /* Streaming scheme (no counterpart in the paper, whose Eq. 4 only states that f*_i(x) moves

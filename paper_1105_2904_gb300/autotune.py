@@ -21,10 +21,11 @@ import os
 
 WIDTHS = (32, 64, 128)
 
-# Velocity error against the FP64 oracle, relative to max|u|, measured by the parity tests
-# (200-300 steps of a suspension): FP64 exact, FP32 deviations 1e-5, FP16 / BF16 scaled
-# deviations 2.4e-4 / 1.8e-3.
-ERROR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 2.4e-4, "bf16": 1.8e-3}
+# Velocity error against the FP64 oracle, relative to max|u|: FP64 exact; FP32 deviations
+# within 1e-5 over 1000 steps (the parity tests' bound; the 512^3 suspension scaled to 64^3
+# and 128^3 measures 2e-6); FP16 / BF16 scaled deviations 3.3e-4 / 2.7e-3 (the bench's
+# 163-step error on the 64^3 sample).
+ERROR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 3.3e-4, "bf16": 2.7e-3}
 
 
 def padded_sites(nx, ny, w):

@@ -23,6 +23,11 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 SO = os.path.join(LIBDIR, "liblbmp.so")
+# The bounds-checked build (-DLBM_DEBUG): kernels check particle ids, record slots and
+# contact-list indices and report LBM_E_BOUNDS through the device status word instead of
+# reading or writing out of range. Built on request only; lbmp loads it when LBMP_DEBUG=1.
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+SO_DEBUG = os.path.join(PKG, "_lib_debug", "liblbmp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -54,25 +59,32 @@ def _sources():
                                                                 os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(SO):
+def up_to_date(so: str = SO) -> bool:
+    if not os.path.exists(so):
         return False
-    t = os.path.getmtime(SO)
+    t = os.path.getmtime(so)
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return SO
-    os.makedirs(BUILD, exist_ok=True)
-    os.makedirs(LIBDIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug=None) -> str:
+    """Builds liblbmp.so (debug=True: the bounds-checked build, SO_DEBUG; None: the build the
+    binding loads, i.e. the bounds-checked one when LBMP_DEBUG=1)."""
+    if debug is None:
+        debug = os.environ.get("LBMP_DEBUG") == "1"
+    so = SO_DEBUG if debug else SO
+    objdir = BUILD_DEBUG if debug else BUILD
+    if not force and up_to_date(so):
+        return so
+    os.makedirs(objdir, exist_ok=True)
+    os.makedirs(os.path.dirname(so), exist_ok=True)
     cc = nvcc()
     procs = []
     objs = []
     for unit, extra in UNITS.items():
-        obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+        obj = os.path.join(objdir, unit.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [cc] + ARCH + COMMON + extra + ["-c", os.path.join(CSRC, unit), "-o", obj]
+        cmd = [cc] + ARCH + COMMON + extra + (["-DLBM_DEBUG"] if debug else []) + \
+            ["-c", os.path.join(CSRC, unit), "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         procs.append((unit, cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -85,11 +97,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(unit)
     if failed:
         raise RuntimeError("nvcc failed for %s" % ", ".join(failed))
-    tmp = SO + ".%d.tmp" % os.getpid()
+    tmp = so + ".%d.tmp" % os.getpid()
     subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
-    os.replace(tmp, SO)
-    return SO
+    os.replace(tmp, so)
+    return so
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug=True if "--debug" in sys.argv else None))

@@ -153,6 +153,22 @@ struct __align__(16) PConst {
 // Device status word values (mirrors lbm_status codes).
 constexpr int ERR_CAPACITY = 8;
 constexpr int ERR_UNSTABLE = 9;
+constexpr int ERR_BOUNDS = 10;
+
+// Index checks of the bounds-checked build (compiled with -DLBM_DEBUG): an index that is out
+// of range records ERR_BOUNDS in the device status word (the first fault wins) and the caller
+// skips or redirects the access; nothing traps. In the normal build the checks compile to
+// nothing (true).
+#ifdef LBM_DEBUG
+__device__ __forceinline__ bool debug_check(int* status, bool ok)
+{
+    if (!ok && status) atomicCAS(status, 0, ERR_BOUNDS);
+    return ok;
+}
+#define LBM_DCHECK(status, ok) ::lbmp::debug_check((status), (ok))
+#else
+#define LBM_DCHECK(status, ok) true
+#endif
 
 // Per-step work-list sizes, cleared at the start of every particle phase.
 struct Counters {
@@ -185,6 +201,8 @@ struct PartView {
     // (bit i), and bit 31 when some source is an IS site of another particle.
     const unsigned* ismask;
     const unsigned* step_id;  // advanced once per step by the particle phase
+    int np;                   // particles (index checks of the LBM_DEBUG build)
+    int* status;              // device status word (the same)
 };
 
 constexpr unsigned MASK_OTHER = 1u << 31;

@@ -289,6 +289,7 @@ __global__ void k_pairs(const ParticleArgs a0, const ParticleArgs* __restrict__ 
     const int xx = cn % 3, yy = (cn / 3) % 3, zz = cn / 9;
     if (xx >= nxc || yy >= nyc || zz >= nzc) return;
     const int cell = (lz[zz] * a.cg.n[1] + ly[yy]) * a.cg.n[0] + lx[xx];
+    if (!LBM_DCHECK(a.status, cell >= 0 && cell < a.cg.total)) return;
     const int s0 = a.cell_start[cell], s1 = a.cell_start[cell + 1];
     if (s0 == s1) return;
     const double ri = a.pc[i].r;
@@ -299,6 +300,7 @@ __global__ void k_pairs(const ParticleArgs a0, const ParticleArgs* __restrict__ 
     }
     for (int s = s0; s < s1; ++s) {
         const int j = a.cell_items[s];
+        if (!LBM_DCHECK(a.status, j >= 0 && j < a.np)) continue;
         if (j <= i) continue;
         double d2 = 0.0;
         for (int k = 0; k < 3; ++k) {
@@ -352,6 +354,7 @@ __global__ void k_resolve(const ParticleArgs a0, const ParticleArgs* __restrict_
     if (threadIdx.x == 0) {
         for (int q = 0; q < n; ++q) {
             const int i = (int)(keys[q] >> 32), j = (int)(keys[q] & 0xffffffffu);
+            if (!LBM_DCHECK(a.status, i >= 0 && i < a.np && j >= 0 && j < a.np)) continue;
             const double ai = a.pc[i].inv_m, aj = a.pc[j].inv_m;
             const double den = ai + aj;
             if (den == 0.0) continue;
@@ -486,6 +489,7 @@ __global__ void k_mark_neighbours(const ParticleArgs a0, const ParticleArgs* __r
                 const int cell = (lz[zz] * a.cg.n[1] + ly[yy]) * a.cg.n[0] + lx[xx];
                 for (int s = a.cell_start[cell]; s < a.cell_start[cell + 1]; ++s) {
                     const int q = a.cell_items[s];
+                    if (!LBM_DCHECK(a.status, q >= 0 && q < a.np)) continue;
                     if (q == p) continue;
                     const double R = rp + a.pc[q].r + 1.0;
                     double d2o = 0.0, d2n = 0.0;

@@ -399,7 +399,7 @@ __device__ __forceinline__ void substitute_is_plain(const Geom& g, const Nbr& n,
         bool bounce;
         pull_source<L, i, WALLS>(g, n, x, y, z, idx, sx, sy, sz, sidx, bounce);
         const unsigned t = pv.tag[sidx];
-        if ((t >> 30) == CLS_IS) {
+        if ((t >> 30) == CLS_IS && LBM_DCHECK(pv.status, (t & PID_MASK) < (unsigned)pv.np)) {
             const PKern& k = pv.pk[t & PID_MASK];
             double r[3], uI[3];
             lever_arm(g, k, sx, sy, sz, r);
@@ -442,7 +442,9 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
     const unsigned mm = m & ~MASK_OTHER;
     const unsigned wm = __reduce_or_sync(__activemask(), mm);
     if (wm) {
-        const PKernF k = pv.pkf[mm ? owner : 0u];
+        unsigned ow = mm ? owner : 0u;
+        if (!LBM_DCHECK(pv.status, ow < (unsigned)pv.np)) ow = 0u;
+        const PKernF k = pv.pkf[ow];
         float r[3], ux[3];
         lever_arm(g, k, x, y, z, r);
         rigid_velocity(k, r, ux);
@@ -515,6 +517,7 @@ __device__ __forceinline__ void substitute_is_other_dev(const Geom& g, const Nbr
             const unsigned sidx = ((unsigned)sz * (unsigned)g.ny + (unsigned)sy) * (unsigned)g.nx + (unsigned)sx;
             const unsigned t = pv.tag[sidx];
             if ((t >> 30) != CLS_IS || (t & PID_MASK) == owner) continue;
+            if (!LBM_DCHECK(pv.status, (t & PID_MASK) < (unsigned)pv.np)) continue;
             const PKernF k = pv.pkf[t & PID_MASK];
             float r[3], us[3];
             lever_arm(g, k, sx, sy, sz, r);
@@ -636,14 +639,16 @@ __device__ __forceinline__ int eq_face_of(const Geom& g, int x, int y, int z)
 // BS transfer of one site in the deviation form (Eqs. 5-7): the forced collision keeps the
 // density and adds F to the momentum, so the post-collision rho_B and rho_B u_B are rho and
 // j + F of the pulled values (mrho, mj). The site takes f^eq(rho_B, u_p + omega_p x r) and
-// its per-site record (dp = rho_B (u_B' - u_B) = rho_B u_B' - (j + F), dl = r x dp, the
-// owner's tag and the step id: one aligned 32-byte sector) feeds the per-particle sums
-// (Eqs. 8-9) that the particle phase takes afterwards in a fixed order.
+// its record (dp = rho_B (u_B' - u_B) = rho_B u_B' - (j + F), dl = r x dp, the owner's tag
+// and the step id: one aligned 32-byte sector at the site's index) feeds the per-particle
+// sums (Eqs. 8-9) that the particle phase takes afterwards in a fixed order.
 template <class L>
 __device__ __forceinline__ void bs_transfer_dev(const SweepArgs& a, int x, int y, int z, unsigned idx, unsigned tagx,
                                                 float mrho, float mj0, float mj1, float mj2, float f[])
 {
-    const PKernF k = a.pv.pkf[tagx & PID_MASK];
+    unsigned pid = tagx & PID_MASK;
+    if (!LBM_DCHECK(a.pv.status, pid < (unsigned)a.pv.np)) pid = 0u;
+    const PKernF k = a.pv.pkf[pid];
     float r[3], ubp[3], dv[6];
     lever_arm(a.g, k, x, y, z, r);
     rigid_velocity(k, r, ubp);
@@ -706,7 +711,7 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
         const bool isbs = valid && (tagx >> 30) == CLS_BS;
         if constexpr (St::deviation) {
             if (isbs) bs_transfer_dev<L>(a, x, y, z, idx, tagx, mrho, mj0, mj1, mj2, f);
-        } else if (isbs) {
+        } else if (isbs && LBM_DCHECK(a.pv.status, (tagx & PID_MASK) < (unsigned)a.pv.np)) {
             C r[3], ub[3], ubp[3], du[3];
             const PKern& k = a.pv.pk[tagx & PID_MASK];
             lever_arm(g, k, x, y, z, r);

@@ -257,8 +257,11 @@ __device__ __forceinline__ void substitute_is_dev2(const Geom& g, const Nbr& n0,
     const unsigned mm0 = m.x & ~MASK_OTHER, mm1 = m.y & ~MASK_OTHER;
     const unsigned wm = __reduce_or_sync(__activemask(), mm0 | mm1);
     if (wm) {
-        const PKernF k0 = pv.pkf[mm0 ? (tags.x & PID_MASK) : 0u];
-        const PKernF k1 = pv.pkf[mm1 ? (tags.y & PID_MASK) : 0u];
+        unsigned w0 = mm0 ? (tags.x & PID_MASK) : 0u, w1 = mm1 ? (tags.y & PID_MASK) : 0u;
+        if (!LBM_DCHECK(pv.status, w0 < (unsigned)pv.np)) w0 = 0u;
+        if (!LBM_DCHECK(pv.status, w1 < (unsigned)pv.np)) w1 = 0u;
+        const PKernF k0 = pv.pkf[w0];
+        const PKernF k1 = pv.pkf[w1];
         float2 r[3], u[3], om[3], ux[3];
         lever_arm2(g, k0, k1, x0, y, z, r);
         kin2(k0, k1, u, om);
@@ -353,9 +356,11 @@ __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int
                                                  float2 f[])
 {
     constexpr int Q = L::Q;
-    const unsigned o0 = tags.x & PID_MASK, o1 = tags.y & PID_MASK;
-    const PKernF k0 = a.pv.pkf[bs0 ? o0 : o1];
-    const PKernF k1 = a.pv.pkf[bs1 ? o1 : o0];
+    unsigned p0 = tags.x & PID_MASK, p1 = tags.y & PID_MASK;
+    if (!LBM_DCHECK(a.pv.status, !bs0 || p0 < (unsigned)a.pv.np)) p0 = 0u;
+    if (!LBM_DCHECK(a.pv.status, !bs1 || p1 < (unsigned)a.pv.np)) p1 = 0u;
+    const PKernF k0 = a.pv.pkf[bs0 ? p0 : p1];
+    const PKernF k1 = a.pv.pkf[bs1 ? p1 : p0];
     float2 r[3], u[3], om[3], ub[3];
     lever_arm2(a.g, k0, k1, x0, y, z, r);
     kin2(k0, k1, u, om);

@@ -13,11 +13,13 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "liblbmp.so")
+# LBMP_DEBUG=1 selects the bounds-checked build (build.build(debug=True)).
+LIB_PATH = os.path.join(_PKG, "_lib_debug" if os.environ.get("LBMP_DEBUG") == "1" else "_lib", "liblbmp.so")
 
 LBM_OK = 0
 STATUS = {0: "LBM_OK", 1: "LBM_E_INVALID", 2: "LBM_E_OOM", 3: "LBM_E_CUDA", 4: "LBM_E_OVERLAP",
-          5: "LBM_E_TIMEOUT", 6: "LBM_E_STATE", 7: "LBM_E_NAN", 8: "LBM_E_CAPACITY", 9: "LBM_E_UNSTABLE"}
+          5: "LBM_E_TIMEOUT", 6: "LBM_E_STATE", 7: "LBM_E_NAN", 8: "LBM_E_CAPACITY", 9: "LBM_E_UNSTABLE",
+          10: "LBM_E_BOUNDS"}
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16DEV, "bf16": LBM_BF16DEV}

@@ -66,3 +66,13 @@ def test_binding_rejects_unknown_names_before_device_use():
     lib = lbmp.load()
     assert lib.lbm_set_streaming(None, 1) == 1
     assert lib.lbm_diagnostics(None, None) == 1
+
+
+def test_bounds_checked_build_compiles_and_exports():
+    # The LBM_DEBUG build (index checks reporting LBM_E_BOUNDS through the device status word)
+    # builds from the same sources and exports the same entry points.
+    so = B.build(debug=True)
+    assert so == B.SO_DEBUG and os.path.exists(so)
+    dbg = ctypes.CDLL(so)
+    for name in declared_functions():
+        assert hasattr(dbg, name), name

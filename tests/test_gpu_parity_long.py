@@ -2,7 +2,10 @@
 
 - FP64 storage after 1000 steps (and the 128x64 fixed-disk channel for its full 2000 steps)
   must agree with the oracle to 1e-12 relative on fields and trajectories.
-- FP32 storage after 1000 steps: velocity within 1e-5 of max|u|, forces within 1e-4.
+- FP32 storage: velocity within 1e-5 of max|u| after 1000 steps (the collision's momentum is
+  exact in FP32, so steady forcing no longer drifts); forces within 1e-4 of max|F| after 300
+  steps and within 2e-4 after 1000 (the coupled particle dynamics amplify FP32 round-off),
+  on a small box and on the 512^3 suspension scaled to 64^3 with the same solid fraction.
 - FP16 / BF16 deviation storage: errors against the oracle are measured and bounded by the
   storage precision (see the bounds below: half keeps 11 significant bits of (f - w)/w,
   bfloat16 keeps 8).
@@ -25,6 +28,7 @@ def _built():
     from paper_1105_2904_gb300 import build as B
     B.build()
     O.build()
+    O.build(openmp=True)
 
 
 def pair(lattice, dims, tau, precision, F=(0, 0, 0), walls=(0, 0, 0), gravity=(0, 0, 0), gap=0.0, bfp=False):
@@ -85,26 +89,48 @@ def test_suspension_fp64_1000_steps():
     assert np.array_equal(g.get_tags(), r.get_tags())
 
 
-@pytest.mark.parametrize("F", [0.0, 1e-6, 1e-5])
-def test_suspension_fp32_long_run(F):
-    # FP32 deviation storage against the FP64 oracle. After 300 steps the velocity field is
-    # within 1e-5 of max|u| and forces within 1e-4 of max|F|. Beyond that the coupled
-    # dynamics amplify FP32 round-off (particles integrate force errors, which feed back into
-    # the fluid), so after 1000 steps the bounds are 1e-4 (velocity) and 1e-3 (force); the
-    # trajectories stay within 1e-5 of a radius throughout.
-    dims, c, rad, d, v, om = _suspension(32, 4, 91)
-    g, r = pair(O.D3Q19, dims, 0.7, "fp32", F=(F, 0, 0), gap=0.5, bfp=True)
-    g.add_particles(c, rad, d, v, om)
-    r.add_particles(c, rad, d, v, om)
-    for steps, (bu, bf) in ((300, (1e-5, 1e-4)), (700, (1e-4, 1e-3))):
+def _fp32_against_oracle(g, r, rad, label):
+    for steps, (bu, bf) in ((300, (1e-5, 1e-4)), (700, (1e-5, 2e-4))):
         g.step(steps)
         r.step(steps)
         rg, ug = g.get_fields()
         rr, ur = r.get_fields()
         pg, pr = g.get_particles(), r.get_particles()
-        assert rel(ug, ur) <= bu, steps
-        assert rel(pg["force"], pr["force"]) <= bf, steps
-        assert np.max(np.abs(pg["x"] - pr["x"]) / np.asarray(rad)[:, None]) <= 1e-5, steps
+        eu, ef = rel(ug, ur), rel(pg["force"], pr["force"])
+        ex = np.max(np.abs(pg["x"] - pr["x"]) / np.asarray(rad)[:, None])
+        print("%s after %d steps: velocity %.2e, force %.2e, position %.2e r" % (label, steps, eu, ef, ex))
+        assert eu <= bu, steps
+        assert ef <= bf, steps
+        assert ex <= 1e-5, steps
+
+
+@pytest.mark.parametrize("F", [0.0, 1e-6, 1e-5])
+def test_suspension_fp32_long_run(F):
+    # FP32 deviation storage against the FP64 oracle over 1000 steps (bounds in the module
+    # docstring); the trajectories stay within 1e-5 of a radius throughout.
+    dims, c, rad, d, v, om = _suspension(32, 4, 91)
+    g, r = pair(O.D3Q19, dims, 0.7, "fp32", F=(F, 0, 0), gap=0.5, bfp=True)
+    g.add_particles(c, rad, d, v, om)
+    r.add_particles(c, rad, d, v, om)
+    _fp32_against_oracle(g, r, rad, "32^3, F = %g" % F)
+
+
+@pytest.mark.parametrize("shape", [16, 0], ids=["two_site", "one_site"])
+def test_suspension_replica_fp32_1000_steps(shape):
+    # The 512^3 suspension (spheres r = 8, 25.6 % solid, tau 0.6, body force 1e-6 on fluid and
+    # particles, density ratio 1.2, velocities N(0, 1e-3)) scaled to 64^3 with the same solid
+    # fraction: 31 spheres. FP32 storage with both sweep kernels against the oracle (its
+    # OpenMP build: the same arithmetic, all cores) over 1000 steps.
+    wl = W.suspension_3d_scaled(64)
+    c, rad, d, v = wl.particles()
+    nx, ny, nz = wl.dims
+    g = lbmp.Simulation(1, nx, ny, nz, wl.tau, body_force=wl.body_force, precision="fp32",
+                        body_force_on_particles=True)
+    g.set_sweep_shape(shape)
+    r = O.OracleSim(1, nx, ny, nz, wl.tau, body_force=wl.body_force, body_force_on_particles=True, openmp=True)
+    g.add_particles(c, rad, d, v)
+    r.add_particles(c, rad, d, v)
+    _fp32_against_oracle(g, r, rad, "64^3 replica, sweep shape %d" % shape)
 
 
 # Storage-precision bounds: the stored quantity is h = (f - w)/w, rounded to 11 (half) or 8

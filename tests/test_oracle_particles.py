@@ -563,3 +563,4 @@ def test_orientation_turns_in_the_space_frame_each_step():
     # the axis did turn, so the order of the rotations matters in this test
     cosang = np.dot(om, om_first) / (np.linalg.norm(om) * np.linalg.norm(om_first))
     assert cosang < 0.99
+
