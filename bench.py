@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--closure-large-cells", type=int, default=0,
                    help="closure workload: also judge the trained network on this many held-out 128^3 "
                         "cells with 200 spheres of radius 3 against their 512^3 radius-12 twins")
+    p.add_argument("--closure-large-train", type=int, default=0,
+                   help="closure workload: also train a network on this many 128^3 / 200-sphere cells "
+                        "and judge it on the held-out large cells")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     p.add_argument("--edge", type=int, default=0, help="override the 3D box edge (same solid fraction)")
     p.add_argument("--sweep-shape", type=int, default=-1,
@@ -59,7 +62,7 @@ def parse():
     p.add_argument("--no-patterns", action="store_true",
                    help="default workload: leave out the 16-bit storages, the batched ensemble and the "
                         "learned closure measured beside the headline line")
-    p.add_argument("--pattern-closure-cells", type=int, nargs=2, default=[256, 32],
+    p.add_argument("--pattern-closure-cells", type=int, nargs=2, default=[384, 48],
                    help="training and held-out cells of the closure measured beside the headline line")
     p.add_argument("--cpu-full", action="store_true",
                    help="also time the all-core oracle on the full-size 3D workload for 10 steps")
@@ -756,10 +759,10 @@ def run_closure(args):
         return
     torch.cuda.set_device(local)
     ntr, nte = args.closure_cells
-    print(json.dumps(measure_closure(ntr, nte, args.closure_large_cells)), flush=True)
+    print(json.dumps(measure_closure(ntr, nte, args.closure_large_cells, args.closure_large_train)), flush=True)
 
 
-def measure_closure(ntr, nte, n_large=0):
+def measure_closure(ntr, nte, n_large=0, n_large_train=0):
     """The closure measurement of run_closure on ntr training and nte held-out cells; returns
     its JSON line. n_large > 0: the trained network is also judged on that many held-out
     cells of the large configuration (128^3 coarse cells with 200 spheres of radius 3, 512^3
@@ -838,6 +841,34 @@ def measure_closure(ntr, nte, n_large=0):
                                    "closure_p95": float(np.percentile(eb_closure, 95))},
             "trained_on": "the %d small cells above (32^3, 8 spheres each)" % ntr,
             "generation_seconds": t_big}
+        if n_large_train > 0:
+            t0 = time.perf_counter()
+            Xl, Tl, cl_c, fl, sl = CL.generate(big, n_large_train, seed=5)
+            t_lg = time.perf_counter() - t0
+            cl2 = CL.Closure(seed=0)
+            cl2.fit(Xl, Tl)
+            e2 = CL.drag_errors(cl2.corrected(Xb, cb, sb), fb)
+            # the coarse and fine runs of the held-out large cells, timed (CUDA events)
+            cells_b = CL.place(big, n_large, seed=3)
+
+            def timed_big(fine):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                torch.cuda.synchronize()
+                ev[0].record()
+                b = CL._run(big, cells_b[:1], fine=fine)
+                ev[1].record()
+                torch.cuda.synchronize()
+                b.close()
+                return ev[0].elapsed_time(ev[1]) / 1e3
+            t_c1, t_f1 = timed_big(False), timed_big(True)
+            line["large_cells"]["trained_on_large_cells"] = {
+                "cells": n_large_train, "samples": int(Xl.shape[0]),
+                "drag_error_vs_fine": {"closure_mean": float(e2.mean()),
+                                       "closure_p95": float(np.percentile(e2, 95)),
+                                       "closure_max": float(e2.max())},
+                "seconds_per_cell": {"coarse": t_c1, "fine": t_f1},
+                "generation_seconds": t_lg}
+            cl2.close()
     cl.close()
     return line
 

@@ -80,35 +80,43 @@ def _run(spec: PairSpec, centers, fine: bool):
     return b
 
 
-def generate(spec: PairSpec, n_cells: int, seed: int):
-    """One batch of coarse / fine pairs. Returns (inputs [N, 4 n_side^3 + 3] CUDA tensor,
+def generate(spec: PairSpec, n_cells: int, seed: int, max_sites: int = 600_000_000):
+    """One set of coarse / fine pairs. Returns (inputs [N, 4 n_side^3 + 3] CUDA tensor,
     targets [N, 6], coarse [N, 6], fine [N, 6], scale [N, 2]) with N = spheres of all cells;
     force rows are (Fx, Fy, Fz, Tx, Ty, Tz), the fine torque already scaled to coarse units;
     targets are (fine - coarse) divided by the Stokes scales 6 pi nu r U and 6 pi nu r^2 U,
-    U the cell's mean fluid velocity along x (scale holds both)."""
+    U the cell's mean fluid velocity along x (scale holds both). The runs go in batches of at
+    most max_sites lattice sites (a 512^3 fine cell holds ~26 GB)."""
     import torch
 
     centers = place(spec, n_cells, seed)
     nu = (spec.tau - 0.5) / 3.0
-    bc = _run(spec, centers, fine=False)
+
+    def chunks(fine):
+        per = max(1, int(max_sites // (spec.L * (spec.factor if fine else 1)) ** 3))
+        return [list(range(i, min(n_cells, i + per))) for i in range(0, n_cells, per)]
+
     feats, coarse, scales = [], [], []
-    for k in range(n_cells):
-        cell = bc.cell(k)
-        rho, u = cell.get_fields()
-        tags = cell.get_tags()
-        U = float(u[..., 0][tags == 0xFFFFFFFF].mean())
-        feats.append(cell.closure_features(spec.n_side, spec.spacing, U))
-        p = cell.get_particles()
-        coarse.append(np.concatenate([p["force"], p["torque"]], axis=1))
-        s_f = 6.0 * math.pi * nu * spec.r * U
-        scales.append(np.tile([s_f, s_f * spec.r], (len(centers[k]), 1)))
-    bc.close()
-    bf = _run(spec, centers, fine=True)
+    for ks in chunks(False):
+        bc = _run(spec, [centers[k] for k in ks], fine=False)
+        for j, k in enumerate(ks):
+            cell = bc.cell(j)
+            rho, u = cell.get_fields()
+            tags = cell.get_tags()
+            U = float(u[..., 0][tags == 0xFFFFFFFF].mean())
+            feats.append(cell.closure_features(spec.n_side, spec.spacing, U))
+            p = cell.get_particles()
+            coarse.append(np.concatenate([p["force"], p["torque"]], axis=1))
+            s_f = 6.0 * math.pi * nu * spec.r * U
+            scales.append(np.tile([s_f, s_f * spec.r], (len(centers[k]), 1)))
+        bc.close()
     fine = []
-    for k in range(n_cells):
-        p = bf.cell(k).get_particles()
-        fine.append(np.concatenate([p["force"], p["torque"] / spec.factor], axis=1))
-    bf.close()
+    for ks in chunks(True):
+        bf = _run(spec, [centers[k] for k in ks], fine=True)
+        for j, k in enumerate(ks):
+            p = bf.cell(j).get_particles()
+            fine.append(np.concatenate([p["force"], p["torque"] / spec.factor], axis=1))
+        bf.close()
     X = torch.cat(feats, 0)
     coarse = np.concatenate(coarse, 0)
     fine = np.concatenate(fine, 0)

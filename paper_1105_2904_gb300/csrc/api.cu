@@ -164,6 +164,7 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     a.tag = ctx->tag;
     a.x = ctx->x;
     a.q = ctx->q;
+    a.xpf = ctx->xpf;
     a.Kold = ctx->Kold;
     a.un = ctx->un;
     a.acc = ctx->acc;
@@ -640,7 +641,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
         }
         cudaFree(p);
     };
-    for (void* p : {(void*)ctx->pk, (void*)ctx->pkf, (void*)ctx->pk_prev, (void*)ctx->pkf_prev, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->q, (void*)ctx->un,
+    for (void* p : {(void*)ctx->pk, (void*)ctx->pkf, (void*)ctx->pk_prev, (void*)ctx->pkf_prev, (void*)ctx->pc, (void*)ctx->tmpl, (void*)ctx->x, (void*)ctx->q, (void*)ctx->xpf, (void*)ctx->un,
                     (void*)ctx->acc, (void*)ctx->force, (void*)ctx->Kold, (void*)ctx->cell_of,
                     (void*)ctx->cell_count, (void*)ctx->cell_start, (void*)ctx->cell_cursor,
                     (void*)ctx->cell_items, (void*)ctx->changed, (void*)ctx->restamp,
@@ -655,6 +656,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CS(dev_alloc(ctx, &ctx->tmpl, sizeof(int) * ctx->h_tmpl.size()));
     CS(dev_alloc(ctx, &ctx->x, sizeof(double) * 3 * np));
     CS(dev_alloc(ctx, &ctx->q, sizeof(double) * 4 * np));
+    CS(dev_alloc(ctx, &ctx->xpf, sizeof(float4) * np));
     CS(dev_alloc(ctx, &ctx->un, sizeof(double) * 3 * np));
     CS(dev_alloc(ctx, &ctx->acc, sizeof(double) * 6 * np));
     CS(dev_alloc(ctx, &ctx->force, sizeof(double) * 6 * np));

@@ -65,6 +65,7 @@ struct lbm_ctx {
     int* tmpl = nullptr;
     double *x = nullptr, *un = nullptr, *acc = nullptr, *force = nullptr;
     double* q = nullptr;       // [np][4] orientation quaternions (w, x, y, z)
+    float4* xpf = nullptr;     // [np] predicted centres in FP32 and radii (contact pre-test)
     int* Kold = nullptr;
     lbmp::Counters* cnt = nullptr;
     int* status = nullptr;

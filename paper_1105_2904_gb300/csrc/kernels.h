@@ -174,6 +174,7 @@ struct ParticleArgs {
     double* q;          // [np][4] orientations, unit quaternions (w, x, y, z)
     int* Kold;          // [np][3] anchor before this step's move
     double* un;         // [np][3] velocity during the contact step
+    float4* xpf;        // [np] predicted centre x + u' in FP32 and the radius (pair pre-test)
     double* acc;        // [np][6]
     double* force;      // [np][6] -dP, -dL of the last step
     const void* bs_scratch;  // per-site dP, dL at BS sites (layout as in SweepArgs)
@@ -224,5 +225,7 @@ void launch_wall_advance(WallVel* wv, int* pending, cudaStream_t s);
 void launch_pack_particles(const ParticleArgs& a, double* out, cudaStream_t s);
 // Opts the contact kernel into the shared memory its pair list needs.
 cudaError_t prepare_particle_kernels(int pair_cap);
+
+
 
 }  // namespace lbmp

@@ -198,11 +198,15 @@ __global__ void k_accel(const ParticleArgs a0, const ParticleArgs* __restrict__ 
         a.acc[(size_t)p * 6 + q] = 0.0;
         a.force[(size_t)p * 6 + q] = -d[q];
     }
+    float xp[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        a.un[(size_t)p * 3 + q] = (k.u[q] - d[q] * pc.inv_m) + pc.ext[q];
+        const double un = (k.u[q] - d[q] * pc.inv_m) + pc.ext[q];
+        a.un[(size_t)p * 3 + q] = un;
         k.om[q] = k.om[q] - d[3 + q] * pc.inv_I;
+        xp[q] = (float)(a.x[(size_t)p * 3 + q] + un);
     }
+    a.xpf[p] = make_float4(xp[0], xp[1], xp[2], (float)pc.r);
     const int c0 = cell_coord(a, 0, a.x[(size_t)p * 3 + 0]);
     const int c1 = cell_coord(a, 1, a.x[(size_t)p * 3 + 1]);
     const int c2 = cell_coord(a, 2, a.x[(size_t)p * 3 + 2]);
@@ -211,34 +215,65 @@ __global__ void k_accel(const ParticleArgs a0, const ParticleArgs* __restrict__ 
     atomicAdd(&a.cell_count[c], 1);
 }
 
-// Exclusive scan of the cell counts (one block).
+// Exclusive scan of the cell counts (one block of 1024 threads). The counts go through shared
+// memory in tiles of 8192: one coalesced load per tile, each thread scans 8 consecutive counts,
+// the threads' totals are scanned with warp shuffles, and the starts are written back
+// coalesced, with a carry from tile to tile (few dependent global-memory round trips, where a
+// thread walking a chunk of the counts serially would pay one per count).
+constexpr int SCAN_T = 1024, SCAN_E = 8, SCAN_TILE = SCAN_T * SCAN_E;
 template <bool B>
-__global__ void k_cell_scan(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
+__global__ void __launch_bounds__(SCAN_T) k_cell_scan(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
     const ParticleArgs a = cell_args<B>(a0, cells);
     if (a.np == 0) return;  // a cell of a batch without particles
-    __shared__ int part[1024];
+    __shared__ int tile[SCAN_TILE];
+    __shared__ int wsum[SCAN_T / 32];
+    __shared__ int carry_s;
     const int n = a.cg.total;
-    const int T = blockDim.x;
-    const int chunk = (n + T - 1) / T;
-    const int b = threadIdx.x * chunk;
-    const int e = min(n, b + chunk);
-    int s = 0;
-    for (int i = b; i < e; ++i) s += a.cell_count[i];
-    part[threadIdx.x] = s;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) carry_s = 0;
     __syncthreads();
-    for (int off = 1; off < T; off <<= 1) {
-        const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    for (int base = 0; base < n; base += SCAN_TILE) {
+        for (int i = t; i < SCAN_TILE; i += SCAN_T) tile[i] = base + i < n ? a.cell_count[base + i] : 0;
         __syncthreads();
-        part[threadIdx.x] += v;
+        int v[SCAN_E], sum = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_E; ++k) {
+            v[k] = tile[t * SCAN_E + k];
+            sum += v[k];
+        }
+        // inclusive scan of the thread sums: within the warp, then across warps
+        int incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        int run = carry + (warp > 0 ? wsum[warp - 1] : 0) + incl - sum;
+#pragma unroll
+        for (int k = 0; k < SCAN_E; ++k) {
+            tile[t * SCAN_E + k] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        for (int i = t; i < SCAN_TILE && base + i < n; i += SCAN_T) a.cell_start[base + i] = tile[i];
+        if (t == SCAN_T - 1) carry_s = carry + wsum[31];
         __syncthreads();
     }
-    int run = part[threadIdx.x] - s;
-    for (int i = b; i < e; ++i) {
-        a.cell_start[i] = run;
-        run += a.cell_count[i];
-    }
-    if (threadIdx.x == T - 1) a.cell_start[n] = part[T - 1];
+    if (t == 0) a.cell_start[n] = carry_s;
 }
 
 template <bool B>
@@ -298,10 +333,32 @@ __global__ void k_pairs(const ParticleArgs a0, const ParticleArgs* __restrict__ 
         xi[k] = a.x[(size_t)i * 3 + k];
         ui[k] = a.un[(size_t)i * 3 + k];
     }
+    const float4 fi = a.xpf[i];
     for (int s = s0; s < s1; ++s) {
         const int j = a.cell_items[s];
         if (!LBM_DCHECK(a.status, j >= 0 && j < a.np)) continue;
         if (j <= i) continue;
+        // FP32 pre-test on the predicted centres: pairs clearly apart skip the FP64 test (GB300's
+        // FP64 pipe is narrow). The margin, half a site plus 1e-6 of the coordinates, is far
+        // above the FP32 rounding of the coordinates (6e-8 of them).
+        {
+            const float4 fj = a.xpf[j];
+            const float dd[3] = {fj.x - fi.x, fj.y - fi.y, fj.z - fi.z};
+            float d2f = 0.0f;
+            for (int k = 0; k < 3; ++k) {
+                float v = dd[k];
+                if (periodic_axis(a.g, k, D)) {
+                    const float n = (float)axis_len(a.g, k);
+                    v -= n * rintf(v / n);
+                }
+                d2f += v * v;
+            }
+            const float big = fmaxf(fmaxf(fmaxf(fabsf(fi.x), fabsf(fi.y)), fabsf(fi.z)),
+                                    fmaxf(fmaxf(fabsf(fj.x), fabsf(fj.y)), fabsf(fj.z)));
+            const float mg = 0.5f + 1e-6f * big;
+            const float Rf = fi.w + fj.w + (float)a.gap + mg;
+            if (d2f > Rf * Rf) continue;
+        }
         double d2 = 0.0;
         for (int k = 0; k < 3; ++k) {
             double pd = (a.x[(size_t)j * 3 + k] + a.un[(size_t)j * 3 + k]) - (xi[k] + ui[k]);
@@ -586,7 +643,7 @@ int particle_phase_a(const ParticleArgs& a0, const ParticleArgs* cells, const Ph
     else
         k_reduce_block<B><<<dim3(sh.max_np, nc), RT, 0, s>>>(a0, cells);
     k_accel<B><<<gp, PT, 0, s>>>(a0, cells);
-    k_cell_scan<B><<<dim3(1, nc), 1024, 0, s>>>(a0, cells);
+    k_cell_scan<B><<<dim3(1, nc), SCAN_T, 0, s>>>(a0, cells);
     k_cell_fill<B><<<gp, PT, 0, s>>>(a0, cells);
     k_pairs<B><<<dim3((sh.max_np * 27 + PT - 1) / PT, nc), PT, 0, s>>>(a0, cells);
     const size_t smem = sizeof(unsigned long long) * (size_t)sh.pair_cap;

@@ -448,21 +448,24 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
         float r[3], ux[3];
         lever_arm(g, k, x, y, z, r);
         rigid_velocity(k, r, ux);
-        const float a0 = ux[1] * k.om[2] - ux[2] * k.om[1];   // u(x) x omega
-        const float a1 = ux[2] * k.om[0] - ux[0] * k.om[2];
-        const float a2 = ux[0] * k.om[1] - ux[1] * k.om[0];
+        // b = u(x) + u(x) x omega
+        const float b0 = ux[0] + (ux[1] * k.om[2] - ux[2] * k.om[1]);
+        const float b1 = ux[1] + (ux[2] * k.om[0] - ux[0] * k.om[2]);
+        const float b2 = ux[2] + (ux[0] * k.om[1] - ux[1] * k.om[0]);
         const float usq = ux[0] * ux[0] + ux[1] * ux[1] + ux[2] * ux[2];
         const float w2 = k.om[0] * k.om[0] + k.om[1] * k.om[1] + k.om[2] * k.om[2];
+        // -1.5 (|u(x)|^2 + |omega|^2 |c|^2) for |c|^2 = 1 and 2
+        const float B1 = -1.5f * (usq + w2), B2 = -1.5f * (usq + 2.0f * w2);
         // rest direction: only an IS site pulls its own rest population, f^eq_0 at u(x)
         if (wm & 1u) {
             const float E = -1.5f * usq;
             const float val = (float)L::w(0) * (E + f[0] * (1.0f + E));
             if (mm & 1u) f[0] = val;
         }
-        // Opposite pair (i, j = opp(i)): with cu = c_i.u(x), ca = c_i.(u(x) x omega),
-        // base = |u(x)|^2 + |omega|^2 |c_i|^2 - (c_i.omega)^2, the sources x - c_i and x - c_j
-        // give E = 4.5 cu^2 - 1.5 base +- 3 (cu + ca) and f = w (E + drho (1 + E)). A
-        // bounced pull (source x itself, stored direction opp) has E = -+3 cu + 4.5 cu^2 - 1.5 |u|^2.
+        // Opposite pair (i, j = opp(i)): with cu = c_i.u(x), cb = c_i.b = cu + c_i.(u(x) x omega)
+        // and cw = c_i.omega, the sources x - c_i and x - c_j give
+        // E = 4.5 cu^2 - 1.5 (|u(x)|^2 + |omega|^2 |c_i|^2 - cw^2) +- 3 cb and f = w (E + drho (1 + E)).
+        // A bounced pull (source x itself, stored direction opp) has E = -+3 cu + 4.5 cu^2 - 1.5 |u|^2.
         sfor<1, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr int j = L::opp(i);
@@ -473,12 +476,10 @@ __device__ __forceinline__ void substitute_is_dev(const Geom& g, const Nbr& n, i
                     constexpr float c2 = cx * cx + cy * cy + cz * cz;
                     constexpr float w = (float)L::w(i);
                     const float cu = cx * ux[0] + cy * ux[1] + cz * ux[2];
-                    const float ca = cx * a0 + cy * a1 + cz * a2;
+                    const float cb = cx * b0 + cy * b1 + cz * b2;
                     const float cw = cx * k.om[0] + cy * k.om[1] + cz * k.om[2];
-                    const float base = usq + w2 * c2 - cw * cw;
-                    const float S = 4.5f * cu * cu - 1.5f * base;
-                    const float D = 3.0f * (cu + ca);
-                    float Ei = S + D, Ej = S - D;
+                    const float S = cu * (4.5f * cu) + (cw * (1.5f * cw) + (c2 == 1.0f ? B1 : B2));
+                    float Ei = S + 3.0f * cb, Ej = S - 3.0f * cb;
                     if constexpr (WALLS) {
                         const float Sb = 4.5f * cu * cu - 1.5f * usq;
                         if (pull_bounces<L, i, WALLS>(n)) Ei = Sb - 3.0f * cu;

@@ -266,12 +266,15 @@ __device__ __forceinline__ void substitute_is_dev2(const Geom& g, const Nbr& n0,
         lever_arm2(g, k0, k1, x0, y, z, r);
         kin2(k0, k1, u, om);
         rigid_velocity2(u, om, r, ux);
-        float2 a[3];  // u(x) x omega
-        a[0] = sub2(mul2(ux[1], om[2]), mul2(ux[2], om[1]));
-        a[1] = sub2(mul2(ux[2], om[0]), mul2(ux[0], om[2]));
-        a[2] = sub2(mul2(ux[0], om[1]), mul2(ux[1], om[0]));
+        float2 b[3];  // u(x) + u(x) x omega
+        b[0] = add2(ux[0], sub2(mul2(ux[1], om[2]), mul2(ux[2], om[1])));
+        b[1] = add2(ux[1], sub2(mul2(ux[2], om[0]), mul2(ux[0], om[2])));
+        b[2] = add2(ux[2], sub2(mul2(ux[0], om[1]), mul2(ux[1], om[0])));
         const float2 usq = fma2(ux[2], ux[2], fma2(ux[1], ux[1], mul2(ux[0], ux[0])));
         const float2 w2 = fma2(om[2], om[2], fma2(om[1], om[1], mul2(om[0], om[0])));
+        // -1.5 (|u(x)|^2 + |omega|^2 |c|^2) for |c|^2 = 1 and 2
+        const float2 usq15 = mul2(p2(-1.5f), usq);
+        const float2 B1 = fma2(p2(-1.5f), w2, usq15), B2 = fma2(p2(-3.0f), w2, usq15);
         if (wm & 1u) {
             const float2 E = mul2(p2(-1.5f), usq);
             const float2 v = mul2(p2((float)L::w(0)), fma2(f[0], add2(E, p2(1.0f)), E));
@@ -287,12 +290,11 @@ __device__ __forceinline__ void substitute_is_dev2(const Geom& g, const Nbr& n0,
                     constexpr float c2 = (float)(L::c(i, 0) * L::c(i, 0) + L::c(i, 1) * L::c(i, 1) + L::c(i, 2) * L::c(i, 2));
                     constexpr float w = (float)L::w(i);
                     const float2 cu = cdot2<L, i>(ux);
-                    const float2 ca = cdot2<L, i>(a);
+                    const float2 cb = cdot2<L, i>(b);
                     const float2 cw = cdot2<L, i>(om);
-                    const float2 base = sub2(fma2(w2, p2(c2), usq), mul2(cw, cw));
-                    const float2 S = fma2(mul2(cu, cu), p2(4.5f), mul2(base, p2(-1.5f)));
-                    const float2 D = mul2(p2(3.0f), add2(cu, ca));
-                    float2 Ei = add2(S, D), Ej = sub2(S, D);
+                    // E = 4.5 cu^2 + 1.5 cw^2 - 1.5 (|u|^2 + |omega|^2 |c|^2) +- 3 cb
+                    const float2 S = fma2(cu, mul2(p2(4.5f), cu), fma2(cw, mul2(p2(1.5f), cw), c2 == 1.0f ? B1 : B2));
+                    float2 Ei = fma2(cb, p2(3.0f), S), Ej = fma2(cb, p2(-3.0f), S);
                     if constexpr (WALLS) {
                         const float2 Sb = fma2(mul2(cu, cu), p2(4.5f), mul2(usq, p2(-1.5f)));
                         const float2 cu3 = mul2(p2(3.0f), cu);
@@ -411,9 +413,13 @@ __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int
     }
 }
 
-// One block: BX threads along x (2 BX sites) times 128 / BX rows of one z-plane.
+// One block: BX threads along x (2 BX sites) times 128 / BX rows of one z-plane. The 16-bit
+// storages run at most 80 registers (six blocks per SM): their sweep is bound by instruction
+// issue at low occupancy, and the cap measured 3.50 -> 3.38 ms at the 512^3 suspension (FP16;
+// seven blocks: 3.46 ms); FP32, bound by memory, keeps five blocks (~95 registers; six blocks
+// measured slower).
 template <class L, typename S, bool WALLS, bool PART, int BX>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep2(const SweepArgs a)
+__global__ void __launch_bounds__(SWEEP_THREADS, sizeof(S) == 2 ? 6 : 5) k_sweep2(const SweepArgs a)
 {
     constexpr int Q = L::Q;
     constexpr int BY = SWEEP_THREADS / BX;

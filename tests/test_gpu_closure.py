@@ -50,18 +50,18 @@ def test_features_match_oracle_stencil_moments(walls):
 def test_trained_closure_beats_the_coarse_method_on_held_out_seeds():
     # Paired coarse (r = 3) / fine (r = 12) runs of the same seeded cells; the network is
     # trained on the GPU on one set of seeds and judged on another. The plain coarse method
-    # misses the fine drag by ~2.4 % on average; trained on 1024 samples the closure must
-    # remove at least 30 % of that error (the measurement's 4096 samples reach ~1 %).
+    # misses the fine drag by ~2.4 % on average; trained on 2048 samples the closure must
+    # remove at least 40 % of that error (measured ~1.0 %; the bench's 3072 samples reach 0.9 %).
     from paper_1105_2904_gb300 import closure as CL
     spec = CL.PairSpec()
-    Xtr, Ttr, ctr, ftr, str_ = CL.generate(spec, 128, seed=1)
+    Xtr, Ttr, ctr, ftr, str_ = CL.generate(spec, 256, seed=1)
     Xte, Tte, cte, fte, ste = CL.generate(spec, 32, seed=2)
-    assert Xtr.shape == (128 * spec.n_spheres, CL.SIZES[0])
+    assert Xtr.shape == (256 * spec.n_spheres, CL.SIZES[0])
     cl = CL.Closure(seed=0)
     losses = cl.fit(Xtr, Ttr)
     assert np.all(np.isfinite(losses)) and losses[-1] < 0.5 * losses[0]
     e_coarse = CL.drag_errors(cte, fte).mean()
     e_closure = CL.drag_errors(cl.corrected(Xte, cte, ste), fte).mean()
     print("held-out mean drag error vs fine: coarse %.4f, coarse + closure %.4f" % (e_coarse, e_closure))
-    assert e_closure <= 0.7 * e_coarse
+    assert e_closure <= 0.6 * e_coarse
     cl.close()
