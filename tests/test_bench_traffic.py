@@ -8,7 +8,7 @@ import pytest
 
 import bench
 
-KEYS = ("sweep_d3q19_fp32", "sweep2_d3q19_fp16", "sweep_inplace_d3q19_fp32", "sweep_batch_ensemble_fp32")
+KEYS = ("sweep2_d3q19_fp32", "sweep2_d3q19_fp16", "sweep_inplace_d3q19_fp32", "sweep_batch_ensemble_fp32")
 
 
 def test_committed_record_is_plausible():
@@ -24,12 +24,12 @@ def test_committed_record_is_plausible():
 
 def test_record_is_dropped_when_the_sources_change(tmp_path, monkeypatch):
     d = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
-    d["sweep_d3q19_fp32"]["source_sha"] = "0" * 16
+    d["sweep2_d3q19_fp32"]["source_sha"] = "0" * 16
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "traffic.json").write_text(json.dumps(d))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "source_sha", lambda: d["sweep2_d3q19_fp16"]["source_sha"])
-    assert bench.traffic_record("sweep_d3q19_fp32") is None
+    assert bench.traffic_record("sweep2_d3q19_fp32") is None
     assert bench.traffic_record("sweep2_d3q19_fp16") is not None
     assert bench.traffic_record("no_such_kernel") is None
