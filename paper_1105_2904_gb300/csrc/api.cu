@@ -60,13 +60,11 @@ lbm_status ensure_alloc(lbm_ctx* ctx)
     CS(dev_alloc(ctx, &ctx->status, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->pending, sizeof(int)));
     CS(dev_alloc(ctx, &ctx->pending_prev, sizeof(int)));
-    CS(dev_alloc(ctx, &ctx->step_id, sizeof(unsigned)));
     CS(dev_alloc(ctx, &ctx->wv, 2 * sizeof(WallVel)));
     CS(dev_alloc(ctx, &ctx->staging, STAGING_BYTES));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(ctx->pending, 0, sizeof(int), ctx->stream));
     CK(cudaMemsetAsync(ctx->pending_prev, 0, sizeof(int), ctx->stream));
-    CK(cudaMemsetAsync(ctx->step_id, 0, sizeof(unsigned), ctx->stream));
     {
         const WallVel w[2] = {wall_vel(ctx), wall_vel(ctx)};
         CK(cudaMemcpyAsync(ctx->wv, w, sizeof(w), cudaMemcpyHostToDevice, ctx->stream));
@@ -174,7 +172,6 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     a.cnt = ctx->cnt;
     a.status = ctx->status;
     a.pending = ctx->pending;
-    a.step_id = ctx->step_id;
     a.cg = ctx->cg;
     a.cell_of = ctx->cell_of;
     a.cell_count = ctx->cell_count;
@@ -214,7 +211,6 @@ PartView part_view(lbm_ctx* ctx)
     v.pkf = ctx->pkf;
     v.pending = ctx->pending;
     v.ismask = ctx->ismask;
-    v.step_id = ctx->step_id;
     v.np = ctx->np;
     v.status = ctx->status;
     return v;
@@ -673,9 +669,7 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
         CS(dev_alloc(ctx, &ctx->cnt, sizeof(Counters)));
         CS(dev_alloc(ctx, &ctx->pairs, sizeof(unsigned long long) * PAIR_CAP));
         CS(dev_alloc(ctx, &ctx->ismask, sizeof(unsigned) * (size_t)ctx->g.N));
-        const size_t rec = ctx->precision == LBM_FP64 ? 6 * sizeof(double) : 8 * sizeof(float);
-        CS(dev_alloc(ctx, (char**)&ctx->bs_scratch, rec * (size_t)ctx->g.N));
-        CK(cudaMemsetAsync(ctx->bs_scratch, 0, rec * (size_t)ctx->g.N, ctx->stream));
+        CS(dev_alloc(ctx, (char**)&ctx->bs_scratch, bs_record_bytes(ctx)));
         CK(prepare_particle_kernels(PAIR_CAP));
     }
     // Cell grid for contact and neighbour searches: cells at least 2 r_max + gap + 4 wide.
@@ -703,6 +697,8 @@ lbm_status lbm_add_particles(lbm_ctx* ctx, int n, const double* centers, const d
     CK(cudaMemsetAsync(ctx->acc, 0, sizeof(double) * 6 * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->force, 0, sizeof(double) * 6 * np, ctx->stream));
     CK(cudaMemsetAsync(ctx->tag, 0xFF, sizeof(unsigned) * (size_t)ctx->g.N, ctx->stream));
+    // no record may carry a BS code before the first sweep writes them
+    CK(cudaMemsetAsync(ctx->bs_scratch, 0, bs_record_bytes(ctx), ctx->stream));
     launch_stamp_all(particle_args(ctx), ctx->stream);
     ctx->kt->update_masks(mask_args(ctx, false), ctx->stream);
     CK(cudaGetLastError());

@@ -2,10 +2,10 @@
 //
 // A checkpoint is the state at a step boundary: the distribution buffer the next sweep reads
 // (in the storage format, IS sites carrying their density), the owner map and the IS-source
-// masks, the particles' kinematic records, positions, orientations and last forces, the pending-imposition
-// flag, the step stamp of the boundary-site records and the wall velocities; with in-place
-// streaming also the layout parity and the IS-site densities the next sweep reads. Everything else
-// a step uses is rebuilt inside the step. The constant part of the set-up (lattice, sizes,
+// masks, the particles' kinematic records, positions, orientations and last forces, the
+// pending-imposition flag and the wall velocities; with in-place streaming also the layout
+// parity and the IS-site densities the next sweep reads. Everything else a step uses is
+// rebuilt inside the step. The constant part of the set-up (lattice, sizes,
 // tau, forces, faces, particle constants and templates) is not stored: it is fingerprinted,
 // and a checkpoint loads only into a context set up with the same calls.
 #include <cstring>
@@ -19,7 +19,7 @@ using namespace lbmp::host;
 namespace {
 
 constexpr char kMagic[8] = {'L', 'B', 'M', 'P', 'C', 'K', 'P', '1'};
-constexpr int kVersion = 4;
+constexpr int kVersion = 5;
 
 struct CkptHeader {
     char magic[8];
@@ -103,7 +103,6 @@ std::vector<Section> sections(lbm_ctx* ctx)
         s.push_back({ctx->force, sizeof(double) * 6 * np});
     }
     s.push_back({ctx->pending, sizeof(int)});
-    s.push_back({ctx->step_id, sizeof(unsigned)});
     s.push_back({ctx->wv, 2 * sizeof(WallVel)});
     return s;
 }
@@ -198,6 +197,9 @@ lbm_status lbm_checkpoint_load(lbm_ctx* ctx, const void* buf, unsigned long long
         CK(cudaMemcpy(s.dev, p, s.bytes, cudaMemcpyHostToDevice));
         p += s.bytes;
     }
+    // the BS records of the context's own past steps may not match the loaded owner map: clear
+    // them (the next sweep rewrites the record of every BS site)
+    if (ctx->np > 0) CK(cudaMemset(ctx->bs_scratch, 0, bs_record_bytes(ctx)));
     ctx->steps = h.steps;
     ctx->stepped = ctx->stepped || h.steps > 0;
     std::memcpy(ctx->uw, h.uw, sizeof(h.uw));

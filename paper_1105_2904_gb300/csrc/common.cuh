@@ -200,7 +200,6 @@ struct PartView {
     // Per-site mask of pull directions whose source is an IS site of the site's own owner
     // (bit i), and bit 31 when some source is an IS site of another particle.
     const unsigned* ismask;
-    const unsigned* step_id;  // advanced once per step by the particle phase
     int np;                   // particles (index checks of the LBM_DEBUG build)
     int* status;              // device status word (the same)
 };

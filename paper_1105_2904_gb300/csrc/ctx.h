@@ -71,7 +71,6 @@ struct lbm_ctx {
     int* status = nullptr;
     int* pending = nullptr;
     int* pending_prev = nullptr;
-    unsigned* step_id = nullptr;
     lbmp::CellGrid cg{};
     int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_cursor = nullptr,
         *cell_items = nullptr;
@@ -156,6 +155,12 @@ void wall_args(const lbm_ctx* ctx, A& a)
 {
     a.moving_walls = ctx->moving_walls ? 1 : 0;
     a.uw = ctx->wv;
+}
+
+// Bytes of the per-site BS records: 6 doubles (FP64 storage) or one float4 per site.
+inline size_t bs_record_bytes(const lbm_ctx* ctx)
+{
+    return (ctx->precision == LBM_FP64 ? 6 * sizeof(double) : sizeof(float4)) * (size_t)ctx->g.N;
 }
 
 const KernelTable* table_for(int precision);

@@ -16,9 +16,8 @@ struct SweepArgs {
     const void* fin;           // [Q][N] storage format
     void* fout;                // [Q][N]
     PartView pv;               // tag == nullptr: no particles
-    void* bs_scratch;          // per-site dP, dL at BS sites: FP64 mode [N][6] doubles; FP32 modes
-                               // [N][8] floats (dP, dL, owner tag bits, step id bits: one 32-byte
-                               // sector)
+    void* bs_scratch;          // per-site BS records: FP64 mode [N][6] doubles (dP, dL); FP32
+                               // modes [N] float4 (dP, owner tag bits: 16 bytes)
     double omega, pre, F[3];   // 1/tau, 1 - 1/(2 tau), body force
     float omega_f, pre_f, F_f[3];  // the same in FP32 (reduced-storage sweeps)
     int moving_walls;          // 1: wall faces may move (uw is read)
@@ -177,12 +176,11 @@ struct ParticleArgs {
     float4* xpf;        // [np] predicted centre x + u' in FP32 and the radius (pair pre-test)
     double* acc;        // [np][6]
     double* force;      // [np][6] -dP, -dL of the last step
-    const void* bs_scratch;  // per-site dP, dL at BS sites (layout as in SweepArgs)
+    void* bs_scratch;        // per-site BS records (layout as in SweepArgs)
     int scratch_f64;         // 1: bs_scratch holds doubles (FP64 mode)
     Counters* cnt;
     int* status;        // device status word (first fault wins)
     int* pending;
-    unsigned* step_id;  // stamps the sweep's per-site records; advanced by the move kernel
     CellGrid cg;
     int* cell_of;       // [np]
     int* cell_count;    // [total]

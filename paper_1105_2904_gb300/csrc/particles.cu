@@ -91,13 +91,17 @@ __global__ void k_reduce_ordered(const ParticleArgs a0, const ParticleArgs* __re
     for (int q = 0; q < 6; ++q) a.acc[(size_t)p * 6 + q] = s[q];
 }
 
-// FP32 modes: one block of 256 threads per particle (a radius-8 sphere's ~890 BS sites in
-// one round of loads). Thread t sums entries t, t + T, ... in FP32 (loads
-// of four entries in flight), then a fixed tree combines the threads (deterministic), and
-// the total is stored in FP64. Each site's 32-byte record holds the id of the particle that
-// owned it as BS in the sweep and the step it was written in, so no owner-map read is
-// needed.
-constexpr int RT = 256;
+// FP32 modes: one block of RT threads per particle. Thread t sums entries t, t + RT, ... in
+// FP32 (loads of four entries in flight), then a fixed tree combines the threads
+// (deterministic), and the total is stored in FP64. A site's 16-byte record holds dp and the
+// owner tag it was written under; the torque dl = r x dp (Eq. 7) is formed here, with
+// r = o - phi from the entry's template offset o (the sweep's lever arm). A record counts when
+// its tag is this particle's BS code: the sweep rewrites the record of every BS site each
+// step, and a site that stops being a BS site of its particle has the tag word of its record
+// cleared at that moment (k_mark_clear, stamp_particle), so a matching record is this step's.
+// The records sit at their sites' indices, so a particle's ~890 come from as many scattered
+// sectors; 128 threads per block measured faster than 256 or 512.
+constexpr int RT = 128;
 template <bool B>
 __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a0, const ParticleArgs* __restrict__ cells)
 {
@@ -108,39 +112,39 @@ __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a0, cons
     if (p >= a.np) return;
     const PConst pc = a.pc[p];
     const int Kw[3] = {a.pk[p].Kw[0], a.pk[p].Kw[1], a.pk[p].Kw[2]};
+    const float phi[3] = {a.pkf[p].phi[0], a.pkf[p].phi[1], a.pkf[p].phi[2]};
     const unsigned code = (CLS_BS << 30) | (unsigned)p;
     const float4* sc = (const float4*)a.bs_scratch;
-    const unsigned sid = *a.step_id;
     float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int e0 = threadIdx.x; e0 < pc.n_bs; e0 += 4 * RT) {
         unsigned site[4];
+        int ent[4];
         bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = e0 + u * RT;
             ok[u] = false;
+            ent[u] = 0;
             if (e < pc.n_bs) {
-                const int ent = a.tmpl[pc.tmpl_off + e];
-                ok[u] = site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site[u]);
+                ent[u] = a.tmpl[pc.tmpl_off + e];
+                ok[u] = site_fast(a.g, Kw, tmpl_ox(ent[u]), tmpl_oy(ent[u]), tmpl_oz(ent[u]), site[u]);
             }
         }
-        float4 v0[4], v1[4];
+        float4 v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            v0[u] = ok[u] ? sc[(size_t)site[u] * 2] : make_float4(0.f, 0.f, 0.f, 0.f);
-            v1[u] = ok[u] ? sc[(size_t)site[u] * 2 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        // the record carries the owner that wrote it and the step: only records written
-        // this step by this particle's own BS sites count
+        for (int u = 0; u < 4; ++u) v[u] = ok[u] ? sc[site[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (ok[u] && __float_as_uint(v1[u].z) == code && __float_as_uint(v1[u].w) == sid) {
-                s[0] += v0[u].x;
-                s[1] += v0[u].y;
-                s[2] += v0[u].z;
-                s[3] += v0[u].w;
-                s[4] += v1[u].x;
-                s[5] += v1[u].y;
+            if (ok[u] && __float_as_uint(v[u].w) == code) {
+                const float r0 = (float)tmpl_ox(ent[u]) - phi[0];
+                const float r1 = (float)tmpl_oy(ent[u]) - phi[1];
+                const float r2 = (float)tmpl_oz(ent[u]) - phi[2];
+                s[0] += v[u].x;
+                s[1] += v[u].y;
+                s[2] += v[u].z;
+                s[3] += r1 * v[u].z - r2 * v[u].y;
+                s[4] += r2 * v[u].x - r0 * v[u].z;
+                s[5] += r0 * v[u].y - r1 * v[u].x;
             }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -156,6 +160,13 @@ __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a0, cons
         for (int w = 0; w < RT / 32; ++w) tot += part[w][threadIdx.x];
         a.acc[(size_t)p * 6 + threadIdx.x] = (double)tot;
     }
+}
+
+// Clears the tag word of a site's FP32 BS record when the site stops being a BS site of the
+// particle that wrote it (the FP64 mode checks the owner map instead).
+__device__ inline void drop_record(const ParticleArgs& a, unsigned site)
+{
+    if (!a.scratch_f64) ((unsigned*)a.bs_scratch)[(size_t)site * 4 + 3] = TAG_FLUID;
 }
 
 // Contact-grid cell of a centre coordinate. FP32 is enough: the cell only selects which
@@ -466,10 +477,7 @@ __global__ void k_move(const ParticleArgs a0, const ParticleArgs* __restrict__ c
     if (a.np == 0) return;  // a cell of a batch without particles
     const int D = a.lattice == 0 ? 2 : 3;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0) {
-        *a.pending = 1;
-        *a.step_id += 1u;
-    }
+    if (p == 0) *a.pending = 1;
     if (p < a.np) {
         const PConst pc = a.pc[p];
         double* u = &a.un[(size_t)p * 3];
@@ -580,7 +588,10 @@ __global__ void k_mark_clear(const ParticleArgs a0, const ParticleArgs* __restri
             unsigned site;
             if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
             const unsigned t = a.tag[site];
-            if (t != TAG_FLUID && (t & PID_MASK) == (unsigned)p) a.tag[site] = TAG_FLUID;
+            if (t != TAG_FLUID && (t & PID_MASK) == (unsigned)p) {
+                a.tag[site] = TAG_FLUID;
+                if ((t >> 30) == CLS_BS) drop_record(a, site);
+            }
         }
     }
 }
@@ -594,7 +605,10 @@ __device__ inline void stamp_particle(const ParticleArgs& a, int p)
         const int ent = a.tmpl[pc.tmpl_off + e];
         unsigned site;
         if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
-        atomicMin(&a.tag[site], (tmpl_cls(ent) << 30) | (unsigned)p);
+        const unsigned code = (tmpl_cls(ent) << 30) | (unsigned)p;
+        const unsigned old = atomicMin(&a.tag[site], code);
+        // a BS site taken over by a lower code is no longer its particle's BS site
+        if (code < old && (old >> 30) == CLS_BS) drop_record(a, site);
     }
 }
 

@@ -640,9 +640,9 @@ __device__ __forceinline__ int eq_face_of(const Geom& g, int x, int y, int z)
 // BS transfer of one site in the deviation form (Eqs. 5-7): the forced collision keeps the
 // density and adds F to the momentum, so the post-collision rho_B and rho_B u_B are rho and
 // j + F of the pulled values (mrho, mj). The site takes f^eq(rho_B, u_p + omega_p x r) and
-// its record (dp = rho_B (u_B' - u_B) = rho_B u_B' - (j + F), dl = r x dp, the owner's tag
-// and the step id: one aligned 32-byte sector at the site's index) feeds the per-particle
-// sums (Eqs. 8-9) that the particle phase takes afterwards in a fixed order.
+// its record (dp = rho_B (u_B' - u_B) = rho_B u_B' - (j + F) and the owner's tag: 16 bytes
+// at the site's index) feeds the per-particle sums (Eqs. 8-9) that the particle phase takes
+// afterwards in a fixed order, forming dl = r x dp there from the site's template offset.
 template <class L>
 __device__ __forceinline__ void bs_transfer_dev(const SweepArgs& a, int x, int y, int z, unsigned idx, unsigned tagx,
                                                 float mrho, float mj0, float mj1, float mj2, float f[])
@@ -650,7 +650,7 @@ __device__ __forceinline__ void bs_transfer_dev(const SweepArgs& a, int x, int y
     unsigned pid = tagx & PID_MASK;
     if (!LBM_DCHECK(a.pv.status, pid < (unsigned)a.pv.np)) pid = 0u;
     const PKernF k = a.pv.pkf[pid];
-    float r[3], ubp[3], dv[6];
+    float r[3], ubp[3], dv[3];
     lever_arm(a.g, k, x, y, z, r);
     rigid_velocity(k, r, ubp);
     const float rho = 1.0f + mrho;
@@ -658,12 +658,7 @@ __device__ __forceinline__ void bs_transfer_dev(const SweepArgs& a, int x, int y
     equilibrium_dev<L>(mrho, ubp, f);
 #pragma unroll
     for (int q = 0; q < 3; ++q) dv[q] = rho * ubp[q] - pB[q];
-    dv[3] = r[1] * dv[2] - r[2] * dv[1];
-    dv[4] = r[2] * dv[0] - r[0] * dv[2];
-    dv[5] = r[0] * dv[1] - r[1] * dv[0];
-    float4* sc = (float4*)a.bs_scratch + (size_t)idx * 2;
-    sc[0] = make_float4(dv[0], dv[1], dv[2], dv[3]);
-    sc[1] = make_float4(dv[4], dv[5], __uint_as_float(tagx), __uint_as_float(*a.pv.step_id));
+    ((float4*)a.bs_scratch)[idx] = make_float4(dv[0], dv[1], dv[2], __uint_as_float(tagx));
 }
 
 // Everything a site does after its populations are pulled: the pending IS imposition,
@@ -829,8 +824,9 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
 }
 
 
+// Deviation storages without walls are held to nine blocks per SM (56 registers, no spills).
 template <class L, typename S, bool WALLS, bool PART>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(const SweepArgs a)
+__global__ void __launch_bounds__(SWEEP_THREADS, (Store<S>::deviation && !WALLS) ? 9 : 1) k_sweep(const SweepArgs a)
 {
     using C = typename Store<S>::C;
     constexpr int Q = L::Q;

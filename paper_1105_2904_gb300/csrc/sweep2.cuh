@@ -393,24 +393,14 @@ __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int
             }
         }
     });
-    // dp = rho_B u_B' - (j + F), dl = r x dp (Eqs. 6-7)
-    float2 dv[6];
+    // dp = rho_B u_B' - (j + F) (Eq. 6); the torque is formed in the particle phase
+    float2 dv[3];
     dv[0] = sub2(mul2(rho, ub[0]), add2(mj0, p2(a.F_f[0])));
     dv[1] = sub2(mul2(rho, ub[1]), add2(mj1, p2(a.F_f[1])));
     dv[2] = sub2(mul2(rho, ub[2]), add2(mj2, p2(a.F_f[2])));
-    dv[3] = sub2(mul2(r[1], dv[2]), mul2(r[2], dv[1]));
-    dv[4] = sub2(mul2(r[2], dv[0]), mul2(r[0], dv[2]));
-    dv[5] = sub2(mul2(r[0], dv[1]), mul2(r[1], dv[0]));
-    const float sid = __uint_as_float(*a.pv.step_id);
-    float4* sc = (float4*)a.bs_scratch + (size_t)idx * 2;
-    if (bs0) {
-        sc[0] = make_float4(dv[0].x, dv[1].x, dv[2].x, dv[3].x);
-        sc[1] = make_float4(dv[4].x, dv[5].x, __uint_as_float(tags.x), sid);
-    }
-    if (bs1) {
-        sc[2] = make_float4(dv[0].y, dv[1].y, dv[2].y, dv[3].y);
-        sc[3] = make_float4(dv[4].y, dv[5].y, __uint_as_float(tags.y), sid);
-    }
+    float4* sc = (float4*)a.bs_scratch + idx;
+    if (bs0) sc[0] = make_float4(dv[0].x, dv[1].x, dv[2].x, __uint_as_float(tags.x));
+    if (bs1) sc[1] = make_float4(dv[0].y, dv[1].y, dv[2].y, __uint_as_float(tags.y));
 }
 
 // One block: BX threads along x (2 BX sites) times 128 / BX rows of one z-plane. The 16-bit
