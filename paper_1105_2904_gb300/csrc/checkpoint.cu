@@ -197,6 +197,9 @@ lbm_status lbm_checkpoint_load(lbm_ctx* ctx, const void* buf, unsigned long long
         CK(cudaMemcpy(s.dev, p, s.bytes, cudaMemcpyHostToDevice));
         p += s.bytes;
     }
+    // a copy from pageable memory may still be in flight when cudaMemcpy returns, and the
+    // library's stream need not be ordered with the copies' stream
+    CK(cudaDeviceSynchronize());
     // the BS records of the context's own past steps may not match the loaded owner map: clear
     // them (the next sweep rewrites the record of every BS site)
     if (ctx->np > 0) CK(cudaMemset(ctx->bs_scratch, 0, bs_record_bytes(ctx)));
