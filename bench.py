@@ -35,14 +35,29 @@ METRIC = "MLUPS"
 UNIT = "MLUPS"
 
 
-def parse():
+def config_defaults(argv):
+    """Option defaults from a JSON file given as --config PATH (keys are the options' names with
+    underscores; options given on the command line still win)."""
+    pre = argparse.ArgumentParser(add_help=False)
+    pre.add_argument("--config")
+    known, _ = pre.parse_known_args(argv)
+    if not known.config:
+        return {}
+    with open(known.config) as f:
+        cfg = json.load(f)
+    return {k: v for k, v in cfg.items() if k != "description"}
+
+
+def parse(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
     p = argparse.ArgumentParser()
+    p.add_argument("--config", help="JSON file of option defaults (bench_configs/)")
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="d3q19_512",
-                   choices=["d3q19_512", "d2q9_sedimentation", "ensemble_64", "closure"])
+                   choices=["d3q19_512", "d2q9_sedimentation", "d2q9_channel_disk", "ensemble_64", "closure"])
     p.add_argument("--closure-cells", type=int, nargs=2, default=[512, 64],
                    help="closure workload: training and held-out cells (8 spheres each)")
     p.add_argument("--closure-large-cells", type=int, default=0,
@@ -66,12 +81,19 @@ def parse():
                    help="training and held-out cells of the closure measured beside the headline line")
     p.add_argument("--cpu-full", action="store_true",
                    help="also time the all-core oracle on the full-size 3D workload for 10 steps")
-    return p.parse_args()
+    cfg = config_defaults(argv)
+    unknown = sorted(set(cfg) - {a.dest for a in p._actions})
+    if unknown:
+        p.error("unknown keys in %s: %s" % (cfg and "--config", ", ".join(unknown)))
+    p.set_defaults(**cfg)
+    return p.parse_args(argv)
 
 
 def workload(args):
     if args.workload == "d2q9_sedimentation":
         return W.sedimentation_2d()
+    if args.workload == "d2q9_channel_disk":
+        return W.channel_disk_2d()
     if args.edge:
         return W.suspension_3d_scaled(args.edge)
     return W.suspension_3d()
@@ -207,14 +229,23 @@ def cpu_baseline(wl, target_s=12.0, configs=()):
         sim = O.OracleSim(O.D3Q19, edge, edge, edge, s.tau, body_force=s.body_force,
                           body_force_on_particles=s.body_force_on_particles)
         sample = "D3Q19 %d^3 periodic, %d spheres r=8 (same solid fraction)" % (edge, len(r))
+    elif wl.sites <= 2 * edge * edge:
+        # a small 2D workload is its own sample
+        s = wl
+        nx2, ny2 = wl.dims[0], wl.dims[1]
+        c, r, d, v = wl.particles()
+        sim = O.OracleSim(O.D2Q9, nx2, ny2, 1, wl.tau, body_force=wl.body_force, walls=wl.walls,
+                          gravity=wl.gravity, gap=0.0)
+        sample = "%s, the whole workload" % wl.name
     else:
         s = wl
+        nx2, ny2 = edge, 2 * edge
         n = max(1, int(round(wl.n_particles * (edge * edge * 2) / wl.sites)))
         c, r = W.rsa_centers((edge, 2 * edge), n, wl.radius, seed=wl.seed, min_gap=wl.min_gap, walls=wl.walls)
         d = np.full(n, wl.density_ratio)
         v = None
-        sim = O.OracleSim(O.D2Q9, edge, 2 * edge, 1, wl.tau, walls=wl.walls, gravity=wl.gravity,
-                          gap=0.0)
+        sim = O.OracleSim(O.D2Q9, edge, 2 * edge, 1, wl.tau, body_force=wl.body_force, walls=wl.walls,
+                          gravity=wl.gravity, gap=0.0)
         sample = "D2Q9 %dx%d closed box, %d disks r=10" % (edge, 2 * edge, n)
     sim.add_particles(c, r, d, v)
     sites = sim.N
@@ -233,8 +264,8 @@ def cpu_baseline(wl, target_s=12.0, configs=()):
         par = O.OracleSim(O.D3Q19, edge, edge, edge, s.tau, body_force=s.body_force,
                           body_force_on_particles=s.body_force_on_particles, openmp=True)
     else:
-        par = O.OracleSim(O.D2Q9, edge, 2 * edge, 1, wl.tau, walls=wl.walls, gravity=wl.gravity,
-                          gap=0.0, openmp=True)
+        par = O.OracleSim(O.D2Q9, nx2, ny2, 1, wl.tau, body_force=wl.body_force, walls=wl.walls,
+                          gravity=wl.gravity, gap=0.0, openmp=True)
     par.add_particles(c, r, d, v)
     par.step(1)
     t = time.perf_counter()
@@ -256,8 +287,8 @@ def cpu_baseline(wl, target_s=12.0, configs=()):
             g = lbmp.Simulation(1, edge, edge, edge, s.tau, body_force=s.body_force, precision=precision,
                                 body_force_on_particles=s.body_force_on_particles, streaming=streaming)
         else:
-            g = lbmp.Simulation(0, edge, 2 * edge, 1, wl.tau, precision=precision, walls=wl.walls,
-                                gravity=wl.gravity, streaming=streaming)
+            g = lbmp.Simulation(0, nx2, ny2, 1, wl.tau, body_force=wl.body_force, precision=precision,
+                                walls=wl.walls, gravity=wl.gravity, streaming=streaming)
         g.set_sweep_shape(shape)
         g.add_particles(c, r, d, v)
         g.step(1 + steps)

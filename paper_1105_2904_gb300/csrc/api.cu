@@ -169,6 +169,7 @@ ParticleArgs particle_args(lbm_ctx* ctx)
     a.force = ctx->force;
     a.bs_scratch = ctx->bs_scratch;
     a.scratch_f64 = ctx->precision == LBM_FP64;
+    a.rec_brick = ctx->precision == LBM_FP32;
     a.cnt = ctx->cnt;
     a.status = ctx->status;
     a.pending = ctx->pending;

@@ -191,6 +191,24 @@ struct Geom {
     int eqface;      // bit f: face f (-x,+x,-y,+y,-z,+z) imposes its velocity by equilibrium
 };
 
+// Index of the FP32 BS record of site (x, y, z). FP32 storage keeps the 16-byte records in
+// bricks of 2 x 2 x 2 sites (2 x 2 x 1 in 2D): a sphere's records then share more DRAM pages
+// than in rows of the whole box, and the per-particle sums read them faster (512^3 suspension:
+// 0.247 -> 0.221 ms per step). The 16-bit storages keep the records at the site index: the
+// index arithmetic costs their instruction-bound sweep more than that.
+__host__ __device__ __forceinline__ unsigned rec_brick_index(const Geom& g, int x, int y, int z)
+{
+    const int zb = g.nz > 1 ? 1 : 0;
+    const unsigned bx = (unsigned)(g.nx + 1) >> 1, by = (unsigned)(g.ny + 1) >> 1;
+    const unsigned brick = ((unsigned)(z >> zb) * by + (unsigned)(y >> 1)) * bx + (unsigned)(x >> 1);
+    return (brick << (2 + zb)) | (((unsigned)z & (unsigned)zb) << 2) | (((unsigned)y & 1u) << 1) | ((unsigned)x & 1u);
+}
+__host__ __device__ __forceinline__ size_t rec_brick_count(const Geom& g)
+{
+    const int zb = g.nz > 1 ? 1 : 0;
+    return ((size_t)((g.nx + 1) >> 1) * (size_t)((g.ny + 1) >> 1) * (size_t)((g.nz + zb) >> zb)) << (2 + zb);
+}
+
 // Everything the sweep and the getters read of the particle side.
 struct PartView {
     const unsigned* tag;  // owner map [N] (nullptr when there are no particles)

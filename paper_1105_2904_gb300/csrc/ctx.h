@@ -157,10 +157,13 @@ void wall_args(const lbm_ctx* ctx, A& a)
     a.uw = ctx->wv;
 }
 
-// Bytes of the per-site BS records: 6 doubles (FP64 storage) or one float4 per site.
+// Bytes of the per-site BS records: 6 doubles (FP64 storage) or one float4 per site (in
+// bricks of 2 x 2 x 2 sites for FP32 storage, rec_brick_index).
 inline size_t bs_record_bytes(const lbm_ctx* ctx)
 {
-    return (ctx->precision == LBM_FP64 ? 6 * sizeof(double) : sizeof(float4)) * (size_t)ctx->g.N;
+    if (ctx->precision == LBM_FP64) return 6 * sizeof(double) * (size_t)ctx->g.N;
+    if (ctx->precision == LBM_FP32) return sizeof(float4) * lbmp::rec_brick_count(ctx->g);
+    return sizeof(float4) * (size_t)ctx->g.N;
 }
 
 const KernelTable* table_for(int precision);

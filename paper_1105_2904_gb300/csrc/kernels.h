@@ -16,8 +16,9 @@ struct SweepArgs {
     const void* fin;           // [Q][N] storage format
     void* fout;                // [Q][N]
     PartView pv;               // tag == nullptr: no particles
-    void* bs_scratch;          // per-site BS records: FP64 mode [N][6] doubles (dP, dL); FP32
-                               // modes [N] float4 (dP, owner tag bits: 16 bytes)
+    void* bs_scratch;          // per-site BS records: FP64 mode [N][6] doubles (dP, dL); other
+                               // modes float4 (dP, owner tag bits: 16 bytes) at the site index
+                               // (16-bit storages) or its brick index (FP32, rec_brick_index)
     double omega, pre, F[3];   // 1/tau, 1 - 1/(2 tau), body force
     float omega_f, pre_f, F_f[3];  // the same in FP32 (reduced-storage sweeps)
     int moving_walls;          // 1: wall faces may move (uw is read)
@@ -178,6 +179,7 @@ struct ParticleArgs {
     double* force;      // [np][6] -dP, -dL of the last step
     void* bs_scratch;        // per-site BS records (layout as in SweepArgs)
     int scratch_f64;         // 1: bs_scratch holds doubles (FP64 mode)
+    int rec_brick;           // 1: float4 records at rec_brick_index (FP32 storage)
     Counters* cnt;
     int* status;        // device status word (first fault wins)
     int* pending;

@@ -127,7 +127,9 @@ __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a0, cons
             ent[u] = 0;
             if (e < pc.n_bs) {
                 ent[u] = a.tmpl[pc.tmpl_off + e];
-                ok[u] = site_fast(a.g, Kw, tmpl_ox(ent[u]), tmpl_oy(ent[u]), tmpl_oz(ent[u]), site[u]);
+                int v[3];
+                ok[u] = site_fast_xyz(a.g, Kw, tmpl_ox(ent[u]), tmpl_oy(ent[u]), tmpl_oz(ent[u]), site[u], v);
+                if (a.rec_brick) site[u] = rec_brick_index(a.g, v[0], v[1], v[2]);
             }
         }
         float4 v[4];
@@ -162,11 +164,14 @@ __global__ void __launch_bounds__(RT) k_reduce_block(const ParticleArgs a0, cons
     }
 }
 
-// Clears the tag word of a site's FP32 BS record when the site stops being a BS site of the
-// particle that wrote it (the FP64 mode checks the owner map instead).
-__device__ inline void drop_record(const ParticleArgs& a, unsigned site)
+// Clears the tag word of the float4 BS record of site (index site, coordinates v) when the site
+// stops being a BS site of the particle that wrote it (the FP64 mode checks the owner map
+// instead).
+__device__ inline void drop_record(const ParticleArgs& a, unsigned site, const int v[3])
 {
-    if (!a.scratch_f64) ((unsigned*)a.bs_scratch)[(size_t)site * 4 + 3] = TAG_FLUID;
+    if (a.scratch_f64) return;
+    const unsigned ri = a.rec_brick ? rec_brick_index(a.g, v[0], v[1], v[2]) : site;
+    ((unsigned*)a.bs_scratch)[(size_t)ri * 4 + 3] = TAG_FLUID;
 }
 
 // Contact-grid cell of a centre coordinate. FP32 is enough: the cell only selects which
@@ -200,27 +205,35 @@ __global__ void k_accel(const ParticleArgs a0, const ParticleArgs* __restrict__ 
     if (a.np == 0) return;  // a cell of a batch without particles
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.np) return;
+    // every load before the first store (see k_move)
     const PConst pc = a.pc[p];
     PKern& k = a.pk[p];
-    double d[6];
+    double d[6], u[3], om[3], x[3];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) d[q] = a.acc[(size_t)p * 6 + q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        u[q] = k.u[q];
+        om[q] = k.om[q];
+        x[q] = a.x[(size_t)p * 3 + q];
+    }
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-        d[q] = a.acc[(size_t)p * 6 + q];
         a.acc[(size_t)p * 6 + q] = 0.0;
         a.force[(size_t)p * 6 + q] = -d[q];
     }
     float xp[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const double un = (k.u[q] - d[q] * pc.inv_m) + pc.ext[q];
+        const double un = (u[q] - d[q] * pc.inv_m) + pc.ext[q];
         a.un[(size_t)p * 3 + q] = un;
-        k.om[q] = k.om[q] - d[3 + q] * pc.inv_I;
-        xp[q] = (float)(a.x[(size_t)p * 3 + q] + un);
+        k.om[q] = om[q] - d[3 + q] * pc.inv_I;
+        xp[q] = (float)(x[q] + un);
     }
     a.xpf[p] = make_float4(xp[0], xp[1], xp[2], (float)pc.r);
-    const int c0 = cell_coord(a, 0, a.x[(size_t)p * 3 + 0]);
-    const int c1 = cell_coord(a, 1, a.x[(size_t)p * 3 + 1]);
-    const int c2 = cell_coord(a, 2, a.x[(size_t)p * 3 + 2]);
+    const int c0 = cell_coord(a, 0, x[0]);
+    const int c1 = cell_coord(a, 1, x[1]);
+    const int c2 = cell_coord(a, 2, x[2]);
     const int c = (c2 * a.cg.n[1] + c1) * a.cg.n[0] + c0;
     a.cell_of[p] = c;
     atomicAdd(&a.cell_count[c], 1);
@@ -452,7 +465,7 @@ __global__ void k_resolve(const ParticleArgs a0, const ParticleArgs* __restrict_
 // about omega / |omega| (space frame), omega the angular velocity after this step's
 // acceleration (Eq. 11) held over dt = 1: q' = dq q, dq = (cos(theta/2), sin(theta/2)
 // omega/|omega|), then divided by its norm. FP64, evaluated as written (-fmad=false).
-__device__ void rotate_orientation(double* q, const double om[3])
+__device__ __forceinline__ void rotate_orientation(double* q, const double om[3])
 {
     const double th = sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
     if (th == 0.0) return;
@@ -479,43 +492,60 @@ __global__ void k_move(const ParticleArgs a0, const ParticleArgs* __restrict__ c
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p == 0) *a.pending = 1;
     if (p < a.np) {
+        // Every load first: the stores below may alias them as far as the compiler knows,
+        // and interleaved they would wait for one memory round trip each.
         const PConst pc = a.pc[p];
-        double* u = &a.un[(size_t)p * 3];
-        double* x = &a.x[(size_t)p * 3];
+        PKern& k = a.pk[p];
+        double* ug = &a.un[(size_t)p * 3];
+        double* xg = &a.x[(size_t)p * 3];
+        double* qg = &a.q[(size_t)p * 4];
+        double u[3] = {ug[0], ug[1], ug[2]};
+        double x[3] = {xg[0], xg[1], xg[2]};
+        const double om[3] = {k.om[0], k.om[1], k.om[2]};
+        const int K0[3] = {k.K[0], k.K[1], k.K[2]};
+        int K[3] = {K0[0], K0[1], K0[2]};
+        int Kw[3] = {k.Kw[0], k.Kw[1], k.Kw[2]};
+        double qv[4] = {qg[0], qg[1], qg[2], qg[3]};
         if (pc.inv_m != 0.0) {
             const double R = pc.r + a.gap;
-            for (int k = 0; k < D; ++k) {
-                if (!a.g.wall[k]) continue;
-                const double xp = x[k] + u[k];
+            for (int d = 0; d < D; ++d) {
+                if (!a.g.wall[d]) continue;
+                const double xp = x[d] + u[d];
                 const double lo = xp + 0.5;
-                const double hi = ((double)axis_len(a.g, k) - 0.5) - xp;
-                if (lo < R && u[k] < 0.0)
-                    u[k] = -u[k];
-                else if (hi < R && u[k] > 0.0)
-                    u[k] = -u[k];
+                const double hi = ((double)axis_len(a.g, d) - 0.5) - xp;
+                if (lo < R && u[d] < 0.0)
+                    u[d] = -u[d];
+                else if (hi < R && u[d] > 0.0)
+                    u[d] = -u[d];
             }
         }
-        PKern& k = a.pk[p];
         bool changed = false;
-        for (int q = 0; q < 3; ++q) k.u[q] = u[q];
-        for (int q = 0; q < 3; ++q) a.Kold[(size_t)p * 3 + q] = k.K[q];
-        for (int q = 0; q < D; ++q) {
-            x[q] = x[q] + u[q];
-            const int s = (int)floor((x[q] - pc.x0[q]) + 0.5);
-            const int Kn = pc.A[q] + s;
-            const int dK = Kn - k.K[q];
+        for (int d = 0; d < D; ++d) {
+            x[d] = x[d] + u[d];
+            const int s = (int)floor((x[d] - pc.x0[d]) + 0.5);
+            const int Kn = pc.A[d] + s;
+            const int dK = Kn - K[d];
             if (dK != 0) changed = true;
             if (dK > 1 || dK < -1) set_status(a.status, ERR_UNSTABLE);
-            k.K[q] = Kn;
-            const int n = axis_len(a.g, q);
-            k.Kw[q] = a.g.wall[q] ? Kn : ((Kn % n) + n) % n;
+            K[d] = Kn;
+            const int n = axis_len(a.g, d);
+            Kw[d] = a.g.wall[d] ? Kn : ((Kn % n) + n) % n;
         }
-        rotate_orientation(&a.q[(size_t)p * 4], k.om);
+        rotate_orientation(qv, om);
+        for (int d = 0; d < 3; ++d) {
+            ug[d] = u[d];
+            xg[d] = x[d];
+            k.u[d] = u[d];
+            a.Kold[(size_t)p * 3 + d] = K0[d];
+            k.K[d] = K[d];
+            k.Kw[d] = Kw[d];
+        }
+        for (int c = 0; c < 4; ++c) qg[c] = qv[c];
         PKernF& kf = a.pkf[p];
-        for (int q = 0; q < 3; ++q) {
-            kf.u[q] = (float)k.u[q];
-            kf.om[q] = (float)k.om[q];
-            kf.Kw[q] = k.Kw[q];
+        for (int d = 0; d < 3; ++d) {
+            kf.u[d] = (float)u[d];
+            kf.om[d] = (float)om[d];
+            kf.Kw[d] = Kw[d];
         }
         if (changed) a.changed[atomicAdd(&a.cnt->nchanged, 1)] = p;
     }
@@ -586,11 +616,12 @@ __global__ void k_mark_clear(const ParticleArgs a0, const ParticleArgs* __restri
         for (int e = threadIdx.x; e < pc.tmpl_n; e += blockDim.x) {
             const int ent = a.tmpl[pc.tmpl_off + e];
             unsigned site;
-            if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+            int v[3];
+            if (!site_fast_xyz(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site, v)) continue;
             const unsigned t = a.tag[site];
             if (t != TAG_FLUID && (t & PID_MASK) == (unsigned)p) {
                 a.tag[site] = TAG_FLUID;
-                if ((t >> 30) == CLS_BS) drop_record(a, site);
+                if ((t >> 30) == CLS_BS) drop_record(a, site, v);
             }
         }
     }
@@ -604,11 +635,12 @@ __device__ inline void stamp_particle(const ParticleArgs& a, int p)
     for (int e = threadIdx.x; e < pc.tmpl_n; e += blockDim.x) {
         const int ent = a.tmpl[pc.tmpl_off + e];
         unsigned site;
-        if (!site_fast(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site)) continue;
+        int v[3];
+        if (!site_fast_xyz(a.g, Kw, tmpl_ox(ent), tmpl_oy(ent), tmpl_oz(ent), site, v)) continue;
         const unsigned code = (tmpl_cls(ent) << 30) | (unsigned)p;
         const unsigned old = atomicMin(&a.tag[site], code);
         // a BS site taken over by a lower code is no longer its particle's BS site
-        if (code < old && (old >> 30) == CLS_BS) drop_record(a, site);
+        if (code < old && (old >> 30) == CLS_BS) drop_record(a, site, v);
     }
 }
 

@@ -641,9 +641,10 @@ __device__ __forceinline__ int eq_face_of(const Geom& g, int x, int y, int z)
 // density and adds F to the momentum, so the post-collision rho_B and rho_B u_B are rho and
 // j + F of the pulled values (mrho, mj). The site takes f^eq(rho_B, u_p + omega_p x r) and
 // its record (dp = rho_B (u_B' - u_B) = rho_B u_B' - (j + F) and the owner's tag: 16 bytes
-// at the site's index) feeds the per-particle sums (Eqs. 8-9) that the particle phase takes
-// afterwards in a fixed order, forming dl = r x dp there from the site's template offset.
-template <class L>
+// at the site's index, or its brick index with BRICK: rec_brick_index) feeds the per-particle
+// sums (Eqs. 8-9) that the particle phase takes afterwards in a fixed order, forming
+// dl = r x dp there from the site's template offset.
+template <class L, bool BRICK>
 __device__ __forceinline__ void bs_transfer_dev(const SweepArgs& a, int x, int y, int z, unsigned idx, unsigned tagx,
                                                 float mrho, float mj0, float mj1, float mj2, float f[])
 {
@@ -658,7 +659,8 @@ __device__ __forceinline__ void bs_transfer_dev(const SweepArgs& a, int x, int y
     equilibrium_dev<L>(mrho, ubp, f);
 #pragma unroll
     for (int q = 0; q < 3; ++q) dv[q] = rho * ubp[q] - pB[q];
-    ((float4*)a.bs_scratch)[idx] = make_float4(dv[0], dv[1], dv[2], __uint_as_float(tagx));
+    const unsigned ri = BRICK ? rec_brick_index(a.g, x, y, z) : idx;
+    ((float4*)a.bs_scratch)[ri] = make_float4(dv[0], dv[1], dv[2], __uint_as_float(tagx));
 }
 
 // Everything a site does after its populations are pulled: the pending IS imposition,
@@ -706,7 +708,8 @@ __device__ __forceinline__ void sweep_site(const SweepArgs& a, int x, int y, int
         // Particle-fluid momentum transfer at BS sites (Eqs. 5-7).
         const bool isbs = valid && (tagx >> 30) == CLS_BS;
         if constexpr (St::deviation) {
-            if (isbs) bs_transfer_dev<L>(a, x, y, z, idx, tagx, mrho, mj0, mj1, mj2, f);
+            if (isbs)
+                bs_transfer_dev<L, std::is_same<S, float>::value>(a, x, y, z, idx, tagx, mrho, mj0, mj1, mj2, f);
         } else if (isbs && LBM_DCHECK(a.pv.status, (tagx & PID_MASK) < (unsigned)a.pv.np)) {
             C r[3], ub[3], ubp[3], du[3];
             const PKern& k = a.pv.pk[tagx & PID_MASK];

@@ -352,7 +352,7 @@ __device__ __forceinline__ void eq_face_half(const float u[3], float drho, float
 // BS transfer (Eqs. 5-7) of the BS sites of the pair on packed pairs: the same expression
 // as bs_transfer_dev; each BS site takes f^eq(rho_B, u_p + omega_p x r) and writes its
 // per-site record.
-template <class L>
+template <class L, bool BRICK>
 __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int y, int z, unsigned idx, uint2 tags,
                                                  bool bs0, bool bs1, float2 mrho, float2 mj0, float2 mj1, float2 mj2,
                                                  float2 f[])
@@ -398,7 +398,8 @@ __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int
     dv[0] = sub2(mul2(rho, ub[0]), add2(mj0, p2(a.F_f[0])));
     dv[1] = sub2(mul2(rho, ub[1]), add2(mj1, p2(a.F_f[1])));
     dv[2] = sub2(mul2(rho, ub[2]), add2(mj2, p2(a.F_f[2])));
-    float4* sc = (float4*)a.bs_scratch + idx;
+    // (x0 is even: the pair's two records are adjacent in either layout)
+    float4* sc = (float4*)a.bs_scratch + (BRICK ? rec_brick_index(a.g, x0, y, z) : idx);
     if (bs0) sc[0] = make_float4(dv[0].x, dv[1].x, dv[2].x, __uint_as_float(tags.x));
     if (bs1) sc[1] = make_float4(dv[0].y, dv[1].y, dv[2].y, __uint_as_float(tags.y));
 }
@@ -449,7 +450,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sizeof(S) == 2 ? 6 : 5) k_sweep
     bool is0 = false, is1 = false;
     if constexpr (PART) {
         const bool bs0 = valid && (tg.x >> 30) == CLS_BS, bs1 = valid && (tg.y >> 30) == CLS_BS;
-        if (bs0 || bs1) bs_transfer_dev2<L>(a, x0, y, z, idx, tg, bs0, bs1, mrho, mj0, mj1, mj2, f);
+        if (bs0 || bs1)
+            bs_transfer_dev2<L, std::is_same<S, float>::value>(a, x0, y, z, idx, tg, bs0, bs1, mrho, mj0, mj1, mj2, f);
         is0 = (tg.x >> 30) == CLS_IS;
         is1 = (tg.y >> 30) == CLS_IS;
         any_is = __any_sync(0xFFFFFFFFu, is0 || is1);

@@ -8,6 +8,7 @@ loudly otherwise, and every call raises ``LbmError`` on a non-OK status.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -544,6 +545,59 @@ class Simulation:
     def diagnostics(self):
         """Total mass and momentum, max |u|, Mach number, non-finite sites (lbm_diagnostics)."""
         return lbm_diagnostics(self.h)
+
+    def run(self, steps, log=None, every=1):
+        """Advances `steps` steps. With `log` (a path, opened for appending, or a text file),
+        writes one JSON line after every `every` steps and after the last: the step count,
+        total mass and fluid momentum, max |u| and Mach number, non-finite sites
+        (lbm_diagnostics), and with particles the summed force and torque on them (-dP_B and
+        -dL_B of Eqs. 8-9, lbm_get_particles). When the state turns non-finite the line is
+        written with "error": "LBM_E_NAN" before the LbmError propagates."""
+        if log is None:
+            self.step(steps)
+            return
+        if every < 1:
+            raise ValueError("every must be at least 1")
+        own = isinstance(log, (str, os.PathLike))
+        f = open(log, "a") if own else log
+        try:
+            done = 0
+            while done < steps:
+                n = min(every, steps - done)
+                self.step(n)
+                done += n
+                rec, err = self._log_record()
+                f.write(json.dumps(rec) + "\n")
+                f.flush()
+                if err is not None:
+                    raise err
+        finally:
+            if own:
+                f.close()
+
+    def _log_record(self):
+        """The JSON record of the current step boundary and the LbmError to raise once it is
+        written (None when the state is finite)."""
+        rec = {"step": int(self.info()["steps"])}
+        err = None
+        try:
+            d = self.diagnostics()
+        except LbmError as e:
+            d = getattr(e, "diagnostics", None)
+            if d is None:
+                raise
+            rec["error"] = STATUS.get(e.status, str(e.status))
+            err = e
+        rec["mass"] = float(d["mass"])
+        rec["momentum"] = [float(v) for v in d["momentum"]]
+        rec["max_speed"] = float(d["max_speed"])
+        rec["mach"] = float(d["mach"])
+        rec["nonfinite_sites"] = int(d["nonfinite_sites"])
+        if err is None and self.np > 0:
+            p = self.get_particles()
+            rec["force_sum"] = [float(v) for v in np.sum(p["force"], axis=0)]
+            rec["torque_sum"] = [float(v) for v in np.sum(p["torque"], axis=0)]
+        return rec, err
 
     def checkpoint(self):
         """State at the current step boundary (lbm_checkpoint_save) as a numpy uint8 array."""

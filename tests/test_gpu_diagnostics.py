@@ -86,3 +86,34 @@ def test_non_finite_values_are_reported(precision):
     g.step(3)
     assert g.diagnostics()["nonfinite_sites"] == 0
     g.close()
+
+
+def test_json_lines_log(tmp_path):
+    import json
+    g = _suspension("pull", "fp32")
+    path = tmp_path / "run.jsonl"
+    g.run(25, log=str(path), every=10)
+    lines = [json.loads(s) for s in path.read_text().splitlines()]
+    assert [r["step"] for r in lines] == [10, 20, 25]
+    last = lines[-1]
+    d = g.diagnostics()
+    p = g.get_particles()
+    assert last["mass"] == d["mass"] and last["max_speed"] == d["max_speed"]
+    assert last["momentum"] == [float(v) for v in d["momentum"]]
+    assert last["force_sum"] == [float(v) for v in p["force"].sum(0)]
+    assert last["torque_sum"] == [float(v) for v in p["torque"].sum(0)]
+    assert all(r["nonfinite_sites"] == 0 and "error" not in r for r in lines)
+    g.close()
+    # a non-finite state (fluid only): the line is written, then the error propagates
+    h = lbmp.Simulation(1, *DIMS, 0.7, body_force=(1e-6, 0.0, 0.0), precision="fp32")
+    h.step(4)
+    f = h.get_f()
+    f[2, 5, 6, 7] = np.inf
+    h.set_f(f)
+    with pytest.raises(lbmp.LbmError) as e:
+        h.run(3, log=str(path), every=3)
+    assert e.value.status == LBM_E_NAN
+    bad = json.loads(path.read_text().splitlines()[-1])
+    assert bad["error"] == "LBM_E_NAN" and bad["nonfinite_sites"] > 0 and bad["step"] == 7
+    assert "force_sum" not in bad
+    h.close()
