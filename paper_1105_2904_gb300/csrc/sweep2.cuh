@@ -32,6 +32,11 @@ template <> struct Pair<__half> {
     {
         return mul2(__half22float2(*reinterpret_cast<const __half2*>(p)), p2(w));
     }
+    // the stored units h = (f - w) / w themselves (the 16-bit sweep computes in them)
+    __device__ static float2 loadh(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
+    __device__ static float loadh1(const __half* p) { return __half2float(*p); }
+    __device__ static void storeh(__half* p, float2 h) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(h); }
+    __device__ static float2 roundh(float2 h) { return __half22float2(__float22half2_rn(h)); }
     __device__ static __half2 pack(float2 g, float w) { return __float22half2_rn(mul2(g, p2(1.0f / w))); }
     __device__ static void store(__half* p, float2 g, float w) { *reinterpret_cast<__half2*>(p) = pack(g, w); }
     __device__ static float2 round(float2 g, float w) { return mul2(__half22float2(pack(g, w)), p2(w)); }
@@ -41,6 +46,16 @@ template <> struct Pair<__nv_bfloat16> {
     {
         return mul2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)), p2(w));
     }
+    __device__ static float2 loadh(const __nv_bfloat16* p)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    __device__ static float loadh1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static void storeh(__nv_bfloat16* p, float2 h)
+    {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(h);
+    }
+    __device__ static float2 roundh(float2 h) { return __bfloat1622float2(__float22bfloat162_rn(h)); }
     __device__ static __nv_bfloat162 pack(float2 g, float w) { return __float22bfloat162_rn(mul2(g, p2(1.0f / w))); }
     __device__ static void store(__nv_bfloat16* p, float2 g, float w)
     {
@@ -69,7 +84,8 @@ __device__ __forceinline__ void pair_neighbours(const Geom& g, int x0, int y, in
 }
 
 // Gathers the populations of both sites (pull propagation with bounce-back): a pair load
-// when both sources are the same pair of another row (c_x = 0), two loads otherwise.
+// when both sources are the same pair of another row (c_x = 0), two loads otherwise. FP32:
+// deviations g = f - w; 16-bit storages: their stored units h = (f - w) / w, unconverted.
 template <class L, typename S, bool WALLS>
 __device__ __forceinline__ void pull2(const S* __restrict__ fin, const Geom& g, const Nbr& n0, const Nbr& n1,
                                       int x0, int y, int z, unsigned idx, float2 f[])
@@ -88,7 +104,9 @@ __device__ __forceinline__ void pull2(const S* __restrict__ fin, const Geom& g, 
         const unsigned row = ((unsigned)sz * (unsigned)g.ny + (unsigned)sy) * (unsigned)g.nx;
         const S* own = fin + (size_t)L::opp(i) * N + idx;  // bounced: the site itself, opp(i)
         if constexpr (cx == 0) {
-            f[i] = brow ? Pair<S>::load(own, w) : Pair<S>::load(fin + (size_t)i * N + row + (unsigned)x0, w);
+            const S* src = brow ? own : fin + (size_t)i * N + row + (unsigned)x0;
+            if constexpr (sizeof(S) == 2) f[i] = Pair<S>::loadh(src);
+            else f[i] = Pair<S>::load(src, w);
         } else {
             // source x - c_x of each site; a wall on x bounces only the site beside it
             const int sx0 = cx > 0 ? n0.xm : x0 + 1;
@@ -100,7 +118,8 @@ __device__ __forceinline__ void pull2(const S* __restrict__ fin, const Geom& g, 
             }
             const S* p0 = b0 ? own : fin + (size_t)i * N + row + (unsigned)sx0;
             const S* p1 = b1 ? own + 1 : fin + (size_t)i * N + row + (unsigned)sx1;
-            f[i] = make_float2(St::load(*p0, w), St::load(*p1, w));
+            if constexpr (sizeof(S) == 2) f[i] = make_float2(Pair<S>::loadh1(p0), Pair<S>::loadh1(p1));
+            else f[i] = make_float2(St::load(*p0, w), St::load(*p1, w));
         }
     });
 }
@@ -108,23 +127,39 @@ __device__ __forceinline__ void pull2(const S* __restrict__ fin, const Geom& g, 
 // BGK collision with Guo forcing (Eq. 3) of both sites on packed pairs; the same expression
 // as collide_dev, one instruction for two sites (CONSERVE: the stored increments' momentum is
 // made exact, as collide_dev<L, true> describes).
-template <class L, bool CONSERVE = false>
+// HS: g holds the scaled deviations h_i = g_i / w_i of the 16-bit storages (their stored units):
+// the moments weigh them by w_i and the update drops the w_i of the equilibrium and forcing
+// terms, which are w_i times an expression in c_i, u and F (the same arithmetic, per unit).
+template <class L, bool CONSERVE = false, bool HS = false>
 __device__ __forceinline__ void collide_dev2(float2 g[], const SweepArgs& a, float2& drho, float2& j0, float2& j1,
                                              float2& j2)
 {
     constexpr int Q = L::Q;
-    drho = g[0];
-    j0 = j1 = j2 = p2(0.0f);
-    sfor<1, Q>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        drho = add2(drho, g[i]);
-        if constexpr (L::c(i, 0) > 0) j0 = add2(j0, g[i]);
-        if constexpr (L::c(i, 0) < 0) j0 = sub2(j0, g[i]);
-        if constexpr (L::c(i, 1) > 0) j1 = add2(j1, g[i]);
-        if constexpr (L::c(i, 1) < 0) j1 = sub2(j1, g[i]);
-        if constexpr (L::c(i, 2) > 0) j2 = add2(j2, g[i]);
-        if constexpr (L::c(i, 2) < 0) j2 = sub2(j2, g[i]);
-    });
+    if constexpr (HS) {
+        drho = mul2(p2((float)L::w(0)), g[0]);
+        j0 = j1 = j2 = p2(0.0f);
+        sfor<1, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr float w = (float)L::w(i);
+            drho = fma2(p2(w), g[i], drho);
+            if constexpr (L::c(i, 0) != 0) j0 = fma2(p2(L::c(i, 0) * w), g[i], j0);
+            if constexpr (L::c(i, 1) != 0) j1 = fma2(p2(L::c(i, 1) * w), g[i], j1);
+            if constexpr (L::c(i, 2) != 0) j2 = fma2(p2(L::c(i, 2) * w), g[i], j2);
+        });
+    } else {
+        drho = g[0];
+        j0 = j1 = j2 = p2(0.0f);
+        sfor<1, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            drho = add2(drho, g[i]);
+            if constexpr (L::c(i, 0) > 0) j0 = add2(j0, g[i]);
+            if constexpr (L::c(i, 0) < 0) j0 = sub2(j0, g[i]);
+            if constexpr (L::c(i, 1) > 0) j1 = add2(j1, g[i]);
+            if constexpr (L::c(i, 1) < 0) j1 = sub2(j1, g[i]);
+            if constexpr (L::c(i, 2) > 0) j2 = add2(j2, g[i]);
+            if constexpr (L::c(i, 2) < 0) j2 = sub2(j2, g[i]);
+        });
+    }
     const float F0 = a.F_f[0], F1 = a.F_f[1], F2 = a.F_f[2];
     const float2 rho = add2(drho, p2(1.0f));
     const float2 inv = make_float2(1.0f / rho.x, 1.0f / rho.y);
@@ -136,7 +171,7 @@ __device__ __forceinline__ void collide_dev2(float2 g[], const SweepArgs& a, flo
     const float2 usq15 = mul2(p2(1.5f), fma2(u2, u2, fma2(u1, u1, mul2(u0, u0))));
     float2 S[3] = {p2(0.0f), p2(0.0f), p2(0.0f)};  // CONSERVE: momentum of the stored increments
     {   // rest direction
-        const float w = (float)L::w(0);
+        const float w = HS ? 1.0f : (float)L::w(0);
         const float2 e = fma2(rho, mul2(usq15, p2(-1.0f)), drho);  // drho - rho usq15
         g[0] = fma2(p2(om1), g[0], fma2(p2(omega * w), e, mul2(p2(-pre * w), uF3)));
     }
@@ -160,7 +195,7 @@ __device__ __forceinline__ void collide_dev2(float2 g[], const SweepArgs& a, flo
             acc(cy, u1);
             acc(cz, u2);
             const float cF = (float)cx * F0 + (float)cy * F1 + (float)cz * F2;
-            const float w = (float)L::w(i);
+            const float w = HS ? 1.0f : (float)L::w(i);
             const float ow = omega * w, pw = pre * w;
             // A = ow (drho + rho (4.5 cu^2 - 1.5 u^2)) + pw (9 cu cF - 3 u.F)
             const float2 q = fma2(mul2(cu, cu), p2(4.5f), mul2(usq15, p2(-1.0f)));
@@ -249,7 +284,28 @@ __device__ __forceinline__ float2 cdot2(const float2 v[3])
 // The pending IS imposition (Eq. 12) for both sites of the pair, on packed pairs: the same
 // expression as substitute_is_dev (density carry: the pulled value is rho_I of its source),
 // each site with its own owner and IS-source mask. Warp-uniform; every lane calls it.
-template <class L, bool WALLS>
+// One site of the pair in the deviation units g of the scalar (one-site) code paths, and back:
+// HS pairs hold h = g / w (a value the scalar path leaves unchanged comes back within an FP32
+// rounding, far below the 16-bit storage's).
+template <class L, bool HS, int H>
+__device__ __forceinline__ void to_g_half(const float2 f[], float fs[])
+{
+    sfor<0, L::Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const float v = half_of<H>(const_cast<float2&>(f[i]));
+        fs[i] = HS ? v * (float)L::w(i) : v;
+    });
+}
+template <class L, bool HS, int H>
+__device__ __forceinline__ void from_g_half(const float fs[], float2 f[])
+{
+    sfor<0, L::Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        half_of<H>(f[i]) = HS ? fs[i] * (1.0f / (float)L::w(i)) : fs[i];
+    });
+}
+
+template <class L, bool WALLS, bool HS = false>
 __device__ __forceinline__ void substitute_is_dev2(const Geom& g, const Nbr& n0, const Nbr& n1, int x0, int y, int z,
                                                    uint2 m, uint2 tags, const PartView& pv, float2 f[])
 {
@@ -277,7 +333,9 @@ __device__ __forceinline__ void substitute_is_dev2(const Geom& g, const Nbr& n0,
         const float2 B1 = fma2(p2(-1.5f), w2, usq15), B2 = fma2(p2(-3.0f), w2, usq15);
         if (wm & 1u) {
             const float2 E = mul2(p2(-1.5f), usq);
-            const float2 v = mul2(p2((float)L::w(0)), fma2(f[0], add2(E, p2(1.0f)), E));
+            // HS: the IS slot holds its density deviation over w_0; the result is in h units
+            const float2 v = HS ? fma2(mul2(p2((float)L::w(0)), f[0]), add2(E, p2(1.0f)), E)
+                                : mul2(p2((float)L::w(0)), fma2(f[0], add2(E, p2(1.0f)), E));
             if (mm0 & 1u) f[0].x = v.x;
             if (mm1 & 1u) f[0].y = v.y;
         }
@@ -303,8 +361,10 @@ __device__ __forceinline__ void substitute_is_dev2(const Geom& g, const Nbr& n0,
                         if (pull_bounces<L, j, WALLS>(n0)) Ej.x = Sb.x + cu3.x;
                         if (pull_bounces<L, j, WALLS>(n1)) Ej.y = Sb.y + cu3.y;
                     }
-                    const float2 vi = mul2(p2(w), fma2(f[i], add2(Ei, p2(1.0f)), Ei));
-                    const float2 vj = mul2(p2(w), fma2(f[j], add2(Ej, p2(1.0f)), Ej));
+                    const float2 vi = HS ? fma2(mul2(p2(w), f[i]), add2(Ei, p2(1.0f)), Ei)
+                                         : mul2(p2(w), fma2(f[i], add2(Ei, p2(1.0f)), Ei));
+                    const float2 vj = HS ? fma2(mul2(p2(w), f[j]), add2(Ej, p2(1.0f)), Ej)
+                                         : mul2(p2(w), fma2(f[j], add2(Ej, p2(1.0f)), Ej));
                     if (mm0 & (1u << i)) f[i].x = vi.x;
                     if (mm1 & (1u << i)) f[i].y = vi.y;
                     if (mm0 & (1u << j)) f[j].x = vj.x;
@@ -316,43 +376,46 @@ __device__ __forceinline__ void substitute_is_dev2(const Geom& g, const Nbr& n0,
     if ((m.x | m.y) & MASK_OTHER) {
         float fs[Q];
         if (m.x & MASK_OTHER) {
-            sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = f[decltype(ic)::value].x; });
+            to_g_half<L, HS, 0>(f, fs);
             substitute_is_other_dev<L, WALLS>(g, n0, x0, y, z, tags.x & PID_MASK, pv, fs);
-            sfor<0, Q>([&](auto ic) { f[decltype(ic)::value].x = fs[decltype(ic)::value]; });
+            from_g_half<L, HS, 0>(fs, f);
         }
         if (m.y & MASK_OTHER) {
-            sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = f[decltype(ic)::value].y; });
+            to_g_half<L, HS, 1>(f, fs);
             substitute_is_other_dev<L, WALLS>(g, n1, x0 + 1, y, z, tags.y & PID_MASK, pv, fs);
-            sfor<0, Q>([&](auto ic) { f[decltype(ic)::value].y = fs[decltype(ic)::value]; });
+            from_g_half<L, HS, 1>(fs, f);
         }
     }
 }
 
 // Moving-wall momentum of the bounced values of one site of the pair.
-template <class L, bool WALLS, int H>
+template <class L, bool WALLS, int H, bool HS = false>
 __device__ __forceinline__ void wall_momentum_half(const SweepArgs& a, const Nbr& n, float2 f[])
 {
     constexpr int Q = L::Q;
     float fs[Q];
-    sfor<0, Q>([&](auto ic) { fs[decltype(ic)::value] = half_of<H>(f[decltype(ic)::value]); });
+    to_g_half<L, HS, H>(f, fs);
     wall_momentum<L, float, WALLS>(n, a.g.eqface, a.uw->uf, fs);
-    sfor<0, Q>([&](auto ic) { half_of<H>(f[decltype(ic)::value]) = fs[decltype(ic)::value]; });
+    from_g_half<L, HS, H>(fs, f);
 }
 
 // Equilibrium-face value f^eq(rho, u) of one site of the pair (deviation form).
-template <class L, int H>
+template <class L, int H, bool HS = false>
 __device__ __forceinline__ void eq_face_half(const float u[3], float drho, float2 f[])
 {
     constexpr int Q = L::Q;
     float fs[Q];
     equilibrium_dev<L>(drho, u, fs);
-    sfor<0, Q>([&](auto ic) { half_of<H>(f[decltype(ic)::value]) = fs[decltype(ic)::value]; });
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        half_of<H>(f[i]) = HS ? fs[i] * (1.0f / (float)L::w(i)) : fs[i];
+    });
 }
 
 // BS transfer (Eqs. 5-7) of the BS sites of the pair on packed pairs: the same expression
 // as bs_transfer_dev; each BS site takes f^eq(rho_B, u_p + omega_p x r) and writes its
 // per-site record.
-template <class L, bool BRICK>
+template <class L, bool BRICK, bool HS = false>
 __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int y, int z, unsigned idx, uint2 tags,
                                                  bool bs0, bool bs1, float2 mrho, float2 mj0, float2 mj1, float2 mj2,
                                                  float2 f[])
@@ -369,8 +432,8 @@ __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int
     rigid_velocity2(u, om, r, ub);
     const float2 rho = add2(mrho, p2(1.0f));
     const float2 usq15 = mul2(p2(1.5f), fma2(ub[2], ub[2], fma2(ub[1], ub[1], mul2(ub[0], ub[0]))));
-    {
-        const float2 e = mul2(p2((float)L::w(0)), fma2(rho, mul2(usq15, p2(-1.0f)), mrho));
+    {   // (HS: in h units, without the w_i factor)
+        const float2 e = mul2(p2(HS ? 1.0f : (float)L::w(0)), fma2(rho, mul2(usq15, p2(-1.0f)), mrho));
         if (bs0) f[0].x = e.x;
         if (bs1) f[0].y = e.y;
     }
@@ -378,7 +441,7 @@ __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int
         constexpr int i = decltype(ic)::value;
         constexpr int j = L::opp(i);
         if constexpr (j > i) {
-            constexpr float w = (float)L::w(i);
+            constexpr float w = HS ? 1.0f : (float)L::w(i);
             const float2 cu = cdot2<L, i>(ub);
             const float2 even = mul2(p2(w), fma2(rho, fma2(mul2(cu, cu), p2(4.5f), mul2(usq15, p2(-1.0f))), mrho));
             const float2 odd = mul2(p2(3.0f * w), mul2(rho, cu));
@@ -408,7 +471,8 @@ __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int
 // storages run at most 80 registers (six blocks per SM): their sweep is bound by instruction
 // issue at low occupancy, and the cap measured 3.50 -> 3.38 ms at the 512^3 suspension (FP16;
 // seven blocks: 3.46 ms); FP32, bound by memory, keeps five blocks (~95 registers; six blocks
-// measured slower).
+// measured slower). The 16-bit storages compute in their stored units h = (f - w) / w, which
+// saves the scaling of every load and store (FP16 sweep 3.350 -> 3.324 ms).
 template <class L, typename S, bool WALLS, bool PART, int BX>
 __global__ void __launch_bounds__(SWEEP_THREADS, sizeof(S) == 2 ? 6 : 5) k_sweep2(const SweepArgs a)
 {
@@ -429,29 +493,32 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sizeof(S) == 2 ? 6 : 5) k_sweep
         tg = *reinterpret_cast<const uint2*>(a.pv.tag + idx);
         mk = *reinterpret_cast<const uint2*>(a.pv.ismask + idx);
     }
+    // 16-bit storages: the pair values stay in the stored units h = (f - w) / w throughout
+    constexpr bool HS = sizeof(S) == 2;
     float2 f[Q];
     pull2<L, S, WALLS>((const S*)a.fin, g, n0, n1, x0, y, z, idx, f);
     if constexpr (PART) {
         if (*a.pv.pending) {
             const uint2 m = make_uint2(tg.x != TAG_FLUID ? mk.x : 0u, tg.y != TAG_FLUID ? mk.y : 0u);
-            substitute_is_dev2<L, WALLS>(g, n0, n1, x0, y, z, m, tg, a.pv, f);
+            substitute_is_dev2<L, WALLS, HS>(g, n0, n1, x0, y, z, m, tg, a.pv, f);
         }
     }
     // A moving wall acts on the bounced value after the IS imposition it may have received.
     if constexpr (WALLS) {
         if (a.moving_walls && *a.pv.pending) {
-            wall_momentum_half<L, WALLS, 0>(a, n0, f);
-            wall_momentum_half<L, WALLS, 1>(a, n1, f);
+            wall_momentum_half<L, WALLS, 0, HS>(a, n0, f);
+            wall_momentum_half<L, WALLS, 1, HS>(a, n1, f);
         }
     }
     float2 mrho, mj0, mj1, mj2;
-    collide_dev2<L, std::is_same<S, float>::value>(f, a, mrho, mj0, mj1, mj2);
+    collide_dev2<L, std::is_same<S, float>::value, HS>(f, a, mrho, mj0, mj1, mj2);
     bool any_is = false;
     bool is0 = false, is1 = false;
     if constexpr (PART) {
         const bool bs0 = valid && (tg.x >> 30) == CLS_BS, bs1 = valid && (tg.y >> 30) == CLS_BS;
         if (bs0 || bs1)
-            bs_transfer_dev2<L, std::is_same<S, float>::value>(a, x0, y, z, idx, tg, bs0, bs1, mrho, mj0, mj1, mj2, f);
+            bs_transfer_dev2<L, std::is_same<S, float>::value, HS>(a, x0, y, z, idx, tg, bs0, bs1, mrho, mj0, mj1,
+                                                                  mj2, f);
         is0 = (tg.x >> 30) == CLS_IS;
         is1 = (tg.y >> 30) == CLS_IS;
         any_is = __any_sync(0xFFFFFFFFu, is0 || is1);
@@ -460,8 +527,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sizeof(S) == 2 ? 6 : 5) k_sweep
     if constexpr (WALLS) {
         if (g.eqface) {
             const int f0 = eq_face_of(g, x0, y, z), f1 = eq_face_of(g, x0 + 1, y, z);
-            if (f0 >= 0 && tg.x == TAG_FLUID) eq_face_half<L, 0>(a.uw[1].uf[f0], mrho.x, f);
-            if (f1 >= 0 && tg.y == TAG_FLUID) eq_face_half<L, 1>(a.uw[1].uf[f1], mrho.y, f);
+            if (f0 >= 0 && tg.x == TAG_FLUID) eq_face_half<L, 0, HS>(a.uw[1].uf[f0], mrho.x, f);
+            if (f1 >= 0 && tg.y == TAG_FLUID) eq_face_half<L, 1, HS>(a.uw[1].uf[f1], mrho.y, f);
         }
     }
     if (!valid) return;
@@ -473,19 +540,28 @@ __global__ void __launch_bounds__(SWEEP_THREADS, sizeof(S) == 2 ? 6 : 5) k_sweep
         float2 dens = p2(0.0f);
         sfor<0, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            dens = add2(dens, Pair<S>::round(f[i], (float)L::w(i)));
+            if constexpr (HS) dens = fma2(p2((float)L::w(i)), Pair<S>::roundh(f[i]), dens);
+            else dens = add2(dens, Pair<S>::round(f[i], (float)L::w(i)));
         });
         sfor<0, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             float2 v = f[i];
-            if (is0) v.x = dens.x;
-            if (is1) v.y = dens.y;
-            Pair<S>::store(fout + (size_t)i * N + idx, v, (float)L::w(i));
+            if constexpr (HS) {
+                const float2 dh = mul2(dens, p2(1.0f / (float)L::w(i)));
+                if (is0) v.x = dh.x;
+                if (is1) v.y = dh.y;
+                Pair<S>::storeh(fout + (size_t)i * N + idx, v);
+            } else {
+                if (is0) v.x = dens.x;
+                if (is1) v.y = dens.y;
+                Pair<S>::store(fout + (size_t)i * N + idx, v, (float)L::w(i));
+            }
         });
     } else {
         sfor<0, Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            Pair<S>::store(fout + (size_t)i * N + idx, f[i], (float)L::w(i));
+            if constexpr (HS) Pair<S>::storeh(fout + (size_t)i * N + idx, f[i]);
+            else Pair<S>::store(fout + (size_t)i * N + idx, f[i], (float)L::w(i));
         });
     }
 }
