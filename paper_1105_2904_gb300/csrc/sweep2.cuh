@@ -19,33 +19,22 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, p2(-1.0f), a); }
 
 // ---- storage pairs -------------------------------------------------------------------------
-// Aligned loads and stores of two consecutive elements, converted to and from the compute
-// form (the deviation g = f - w) exactly as Store<S>::load / save convert one element.
+// Aligned loads and stores of two consecutive elements: FP32 storage in its compute form, the
+// deviation g = f - w (as Store<float>); the 16-bit storages in their stored units.
 template <typename S> struct Pair;
 template <> struct Pair<float> {
     __device__ static float2 load(const float* p, float) { return *reinterpret_cast<const float2*>(p); }
     __device__ static void store(float* p, float2 g, float) { *reinterpret_cast<float2*>(p) = g; }
     __device__ static float2 round(float2 g, float) { return g; }
 };
+// The 16-bit storages: the two-site sweep computes in their stored units h = (f - w) / w.
 template <> struct Pair<__half> {
-    __device__ static float2 load(const __half* p, float w)
-    {
-        return mul2(__half22float2(*reinterpret_cast<const __half2*>(p)), p2(w));
-    }
-    // the stored units h = (f - w) / w themselves (the 16-bit sweep computes in them)
     __device__ static float2 loadh(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
     __device__ static float loadh1(const __half* p) { return __half2float(*p); }
     __device__ static void storeh(__half* p, float2 h) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(h); }
     __device__ static float2 roundh(float2 h) { return __half22float2(__float22half2_rn(h)); }
-    __device__ static __half2 pack(float2 g, float w) { return __float22half2_rn(mul2(g, p2(1.0f / w))); }
-    __device__ static void store(__half* p, float2 g, float w) { *reinterpret_cast<__half2*>(p) = pack(g, w); }
-    __device__ static float2 round(float2 g, float w) { return mul2(__half22float2(pack(g, w)), p2(w)); }
 };
 template <> struct Pair<__nv_bfloat16> {
-    __device__ static float2 load(const __nv_bfloat16* p, float w)
-    {
-        return mul2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p)), p2(w));
-    }
     __device__ static float2 loadh(const __nv_bfloat16* p)
     {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
@@ -56,12 +45,6 @@ template <> struct Pair<__nv_bfloat16> {
         *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(h);
     }
     __device__ static float2 roundh(float2 h) { return __bfloat1622float2(__float22bfloat162_rn(h)); }
-    __device__ static __nv_bfloat162 pack(float2 g, float w) { return __float22bfloat162_rn(mul2(g, p2(1.0f / w))); }
-    __device__ static void store(__nv_bfloat16* p, float2 g, float w)
-    {
-        *reinterpret_cast<__nv_bfloat162*>(p) = pack(g, w);
-    }
-    __device__ static float2 round(float2 g, float w) { return mul2(__bfloat1622float2(pack(g, w)), p2(w)); }
 };
 
 // Component h (0: site x0, 1: site x0 + 1) of a pair.
