@@ -467,9 +467,20 @@ __global__ void k_resolve(const ParticleArgs a0, const ParticleArgs* __restrict_
 // omega/|omega|), then divided by its norm. FP64, evaluated as written (-fmad=false).
 __device__ __forceinline__ void rotate_orientation(double* q, const double om[3])
 {
-    const double th = sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
-    if (th == 0.0) return;
-    const double c = cos(0.5 * th), sn = sin(0.5 * th) / th;
+    const double t2 = om[0] * om[0] + om[1] * om[1] + om[2] * om[2];  // theta^2
+    if (t2 == 0.0) return;
+    double c, sn;  // cos(theta / 2) and sin(theta / 2) / theta
+    if (t2 < 1e-4) {
+        // below theta = 0.01 (every suspension here turns by far less per step) their Taylor
+        // series in theta^2 to the third order; the first term left out is below 1e-23, and GB300's
+        // narrow FP64 pipe spends most of this kernel on cos, sin and the division otherwise
+        c = 1.0 + t2 * (-1.0 / 8.0 + t2 * (1.0 / 384.0 + t2 * (-1.0 / 46080.0)));
+        sn = 0.5 + t2 * (-1.0 / 48.0 + t2 * (1.0 / 3840.0 + t2 * (-1.0 / 645120.0)));
+    } else {
+        const double th = sqrt(t2);
+        c = cos(0.5 * th);
+        sn = sin(0.5 * th) / th;
+    }
     const double d[4] = {c, sn * om[0], sn * om[1], sn * om[2]};
     const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
     double r[4];
