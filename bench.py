@@ -80,7 +80,10 @@ def parse(argv=None):
     p.add_argument("--pattern-closure-cells", type=int, nargs=2, default=[384, 48],
                    help="training and held-out cells of the closure measured beside the headline line")
     p.add_argument("--cpu-full", action="store_true",
-                   help="also time the all-core oracle on the full-size 3D workload for 10 steps")
+                   help="also time the all-core oracle on the full-size 3D workload for 10 steps "
+                        "(on by default for the default 512^3 workload)")
+    p.add_argument("--no-cpu-full", action="store_true",
+                   help="leave out the full-size oracle timing of the default workload (~2 minutes)")
     cfg = config_defaults(argv)
     unknown = sorted(set(cfg) - {a.dest for a in p._actions})
     if unknown:
@@ -497,7 +500,8 @@ def run_ours(args):
             configs += [("fp16", -1, "pull"), ("bf16", -1, "pull")]
         cpu, errs = cpu_baseline(wl, configs=configs)
         err = errs[0]
-        if args.cpu_full and lattice == 1:
+        full = args.cpu_full or (args.workload == "d3q19_512" and not args.edge)
+        if full and not args.no_cpu_full and lattice == 1:
             cpu["full_size"] = cpu_full_size(wl)
 
     patterns = None
