@@ -450,14 +450,14 @@ __device__ __forceinline__ void bs_transfer_dev2(const SweepArgs& a, int x0, int
     if (bs1) sc[1] = make_float4(dv[0].y, dv[1].y, dv[2].y, __uint_as_float(tags.y));
 }
 
-// One block: BX threads along x (2 BX sites) times 128 / BX rows of one z-plane. The 16-bit
-// storages run at most 80 registers (six blocks per SM): their sweep is bound by instruction
-// issue at low occupancy, and the cap measured 3.50 -> 3.38 ms at the 512^3 suspension (FP16;
-// seven blocks: 3.46 ms); FP32, bound by memory, keeps five blocks (~95 registers; six blocks
-// measured slower). The 16-bit storages compute in their stored units h = (f - w) / w, which
-// saves the scaling of every load and store (FP16 sweep 3.350 -> 3.324 ms).
+// One block: BX threads along x (2 BX sites) times 128 / BX rows of one z-plane, five blocks per
+// SM (96 registers, no spills). The 16-bit storages compute in their stored units
+// h = (f - w) / w, which saves the scaling of every load and store (FP16 sweep 3.350 -> 3.324 ms
+// at the 512^3 suspension); with that and the IS-source masks loaded only at solid pairs they
+// run best at five blocks as well (3.225 ms at six blocks and 80 registers, with spills; seven
+// blocks spill far more), as FP32 always did (six blocks measured slower).
 template <class L, typename S, bool WALLS, bool PART, int BX>
-__global__ void __launch_bounds__(SWEEP_THREADS, sizeof(S) == 2 ? 6 : 5) k_sweep2(const SweepArgs a)
+__global__ void __launch_bounds__(SWEEP_THREADS, 5) k_sweep2(const SweepArgs a)
 {
     constexpr int Q = L::Q;
     constexpr int BY = SWEEP_THREADS / BX;
