@@ -422,10 +422,10 @@ __global__ void k_resolve(const ParticleArgs a0, const ParticleArgs* __restrict_
                 const int u = t ^ stride;
                 if (u > t) {
                     const bool up = (t & size) == 0;
-                    const unsigned long long A = keys[t], B = keys[u];
-                    if ((A > B) == up) {
-                        keys[t] = B;
-                        keys[u] = A;
+                    const unsigned long long kt = keys[t], ku = keys[u];
+                    if ((kt > ku) == up) {
+                        keys[t] = ku;
+                        keys[u] = kt;
                     }
                 }
             }
